@@ -1,0 +1,408 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: counts the
+paper prints, closed forms, invariants of the reflection group, library
+routines (numpy's Chebyshev module, SVD), brute force on tiny inputs, and the
+convergence of the whole FMM to the direct sum.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as o
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden():
+    with open(os.path.join(GOLDEN, "paper_counts.json")) as f:
+        return json.load(f)
+
+
+def _signed_perms():
+    """All 48 signed axis permutations as 3x3 integer matrices (brute force)."""
+    out = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1, -1), repeat=3):
+            M = np.zeros((3, 3), dtype=int)
+            for r in range(3):
+                M[r, perm[r]] = signs[r]
+            out.append(M)
+    return out
+
+
+# ---------------------------------------------------------------- counts
+def test_paper_counts():
+    g = _golden()
+    T = o.transfer_vectors()
+    assert len(T) == g["distinct_transfer_vectors_per_level"]["value"]
+    assert len(o.t_sym_list()) == g["unique_operators_bbfmm"]["value"]
+    near = [t for t in itertools.product(range(-1, 2), repeat=3)]
+    assert len(near) == g["near_field_per_cell"]["value"]
+    # an interior cell at level 4: its list holds the 216 children of the parent's
+    # 27 neighbours minus its own 27 neighbours
+    cells = o.full_grid_cells(4)
+    off, src = o.interaction_lists(cells, cells)
+    sizes = np.diff(off)
+    assert sizes.max() == g["max_far_per_cell"]["value"]
+    assert g["children_near_and_far"]["value"] - g["near_field_per_cell"]["value"] == sizes.max()
+    flips = {o.g_index(t) % 8 for t in T}
+    orders = {o.g_index(t) // 8 for t in T}
+    assert len(flips) == g["axial_octants"]["value"]
+    assert len(orders) == g["diagonal_cones"]["value"]
+
+
+def test_tsym_is_orbit_representatives():
+    """T_sym holds exactly one vector of each orbit of T under the 48 reflections."""
+    T = set(o.transfer_vectors())
+    G = _signed_perms()
+    orbits = set()
+    for t in T:
+        orbits.add(frozenset(tuple(int(v) for v in M @ np.array(t)) for M in G))
+    assert sum(len(orb) for orb in orbits) == len(T) == 316
+    tsym = o.t_sym_list()
+    assert len(orbits) == len(tsym)
+    for orb in orbits:
+        reps = [t for t in orb if t in tsym]
+        assert len(reps) == 1
+        for t in orb:
+            assert o.p_vector(t) == reps[0]
+    # multiplicities n_p of Alg. 2 are orbit sizes 48 / |stabiliser|
+    mult = {o.p_vector(t): 0 for t in T}
+    for t in T:
+        mult[o.p_vector(t)] += 1
+    for p, n in mult.items():
+        stab = sum(1 for M in G if tuple(int(v) for v in M @ np.array(p)) == p)
+        assert n * stab == 48
+
+
+def test_level_totals_closed_form():
+    """Full-grid list totals equal A^3 - B^3 with per-axis pair counts (separability)."""
+    for L in (2, 3, 4):
+        n = 1 << L
+        A = sum(1 for x in range(n) for y in range(n) if abs((x >> 1) - (y >> 1)) <= 1)
+        B = sum(1 for x in range(n) for y in range(n) if abs(x - y) <= 1)
+        cells = o.full_grid_cells(L)
+        off, src = o.interaction_lists(cells, cells)
+        assert off[-1] == A ** 3 - B ** 3
+    # the level-3 total is the config-1 interaction count
+    assert (40 ** 3 - 22 ** 3) == 53352
+
+
+def test_lists_match_brute_force_on_pruned_level():
+    """Candidate enumeration equals the all-pairs admissibility test (level 3, pruned)."""
+    rng = np.random.default_rng(11)
+    cells = o.full_grid_cells(3)
+    keep = rng.random(len(cells)) < 0.6
+    cells = cells[keep]
+    off, src = o.interaction_lists(cells, cells)
+    for x in range(len(cells)):
+        brute = [y for y in range(len(cells))
+                 if o.is_far_pair(tuple(cells[x]), tuple(cells[y]))]
+        assert list(src[off[x]:off[x + 1]]) == brute
+
+
+# ---------------------------------------------------------------- nodes
+def test_chebyshev_roots_closed_forms():
+    assert np.allclose(o.cheb_roots(1), [0.0])
+    assert np.allclose(o.cheb_roots(2), [-1 / np.sqrt(2), 1 / np.sqrt(2)], rtol=0, atol=1e-15)
+    assert np.allclose(o.cheb_roots(3), [-np.sqrt(3) / 2, 0.0, np.sqrt(3) / 2], rtol=0, atol=1e-15)
+    for ell in range(1, 10):
+        r = o.cheb_roots(ell)
+        assert np.all(np.diff(r) > 0)
+        coef = np.zeros(ell + 1)
+        coef[ell] = 1.0
+        assert np.max(np.abs(np.polynomial.chebyshev.chebval(r, coef))) < 1e-13
+        ref = np.sort(np.polynomial.chebyshev.chebroots(coef))
+        assert np.allclose(r, ref, rtol=0, atol=1e-12)
+
+
+def test_index_map_x_fastest():
+    for ell in (2, 3, 5):
+        mi = o.multi_indices(ell)
+        assert len({tuple(r) for r in mi}) == ell ** 3
+        assert tuple(mi[1]) == (1, 0, 0)
+        assert tuple(mi[ell]) == (0, 1, 0)
+        assert tuple(mi[ell * ell]) == (0, 0, 1)
+        for j in range(ell ** 3):
+            assert o.m_of(mi[j], ell) == j
+
+
+def test_lagrange_basis_properties():
+    for ell in (2, 3, 5, 7):
+        xi = o.cheb_roots(ell)
+        assert np.allclose(o.lagrange_1d(ell, xi), np.eye(ell), atol=1e-13)
+        x = np.linspace(-1, 1, 37)
+        L = o.lagrange_1d(ell, x)
+        assert np.allclose(L.sum(axis=1), 1.0, atol=1e-12)
+
+
+def test_interpolation_exact_below_degree_ell():
+    """S_ell reproduces tensor polynomials of degree < ell per axis (Eq. (2))."""
+    rng = np.random.default_rng(3)
+    for ell in (3, 4, 6):
+        center, w = np.array([0.3, -0.2, 0.1]), 0.5
+        nodes = o.cell_nodes(ell, center, w)
+        pts = center + 0.5 * w * rng.uniform(-1, 1, (50, 3))
+        S = o.interp_matrix(ell, pts, center, w)
+        for deg in itertools.product(range(ell), repeat=3):
+            f = lambda p: np.prod(p ** np.array(deg), axis=1)
+            assert np.allclose(S @ f(nodes), f(pts), rtol=1e-10, atol=1e-12)
+        # one degree higher is not reproduced
+        f = lambda p: p[:, 0] ** ell
+        assert np.max(np.abs(S @ f(nodes) - f(pts))) > 1e-6
+
+
+def test_m2m_equals_direct_p2m_to_parent():
+    rng = np.random.default_rng(5)
+    ell = 4
+    pts = rng.uniform(-1, 1, (400, 3))
+    q = rng.standard_normal(400)
+    cells4, W4 = o.p2m(ell, 4, pts, q)
+    parents, W3 = o.m2m(ell, cells4, W4)
+    cells3, W3d = o.p2m(ell, 3, pts, q)
+    assert np.array_equal(parents, cells3)
+    assert np.allclose(W3, W3d, rtol=1e-11, atol=1e-11)
+
+
+# ---------------------------------------------------------------- symmetry
+def test_model_example_2d():
+    """The 2-D model example of Sec. 4.2.1 (Fig. 1, Fig. 2), embedded with t3 = 0."""
+    g = _golden()["model_example_2d"]
+    ell = g["ell"]
+    ref, ax, dg, comb = (tuple(g[k]) + (0,) for k in ("t_ref", "t_axial", "t_diag", "t_combined"))
+    assert o.p_vector(ax) == ref and o.p_vector(dg) == ref and o.p_vector(comb) == ref
+    mi = o.multi_indices(ell)
+    flip1 = [o.m_of((ell - 1 - a[0], a[1], a[2]), ell) for a in mi]      # Eq. (21)
+    swap12 = [o.m_of((a[1], a[0], a[2]), ell) for a in mi]              # Eq. (22)
+    assert list(o.sigma_of_t(ax, ell)) == flip1
+    assert list(o.sigma_of_t(dg, ell)) == swap12
+    # (-1, 2): axial flip first, then the diagonal swap (reflections do not commute)
+    first_flip_then_swap = [o.m_of((a[1], ell - 1 - a[0], a[2]), ell) for a in mi]
+    first_swap_then_flip = [o.m_of((ell - 1 - a[1], a[0], a[2]), ell) for a in mi]
+    assert list(o.sigma_of_t(comb, ell)) == first_flip_then_swap
+    assert first_flip_then_swap != first_swap_then_flip
+    for level in (2, 3):
+        Kr = o.operator_for_t(ell, 0, 0.0, level, ref)
+        for t in (ax, dg, comb):
+            s = o.sigma_of_t(t, ell)
+            Kt = o.operator_for_t(ell, 0, 0.0, level, t)
+            assert np.allclose(Kt, Kr[np.ix_(s, s)], rtol=1e-14, atol=0)
+            # entries themselves differ before the permutation (Sec. 4.2.1)
+            assert not np.allclose(Kt, Kr, rtol=1e-6)
+
+
+def test_sigma_tables_group_properties():
+    for ell in (2, 3, 4, 5):
+        T = o.transfer_vectors()
+        tab = o.sigma_tables(ell)
+        assert tab.shape == (48, ell ** 3)
+        for g in range(48):
+            assert sorted(tab[g]) == list(range(ell ** 3))
+        assert len({tuple(r) for r in tab}) == 48
+        for t in T:
+            assert np.array_equal(o.sigma_of_t(t, ell), tab[o.g_index(t)])
+            if o.in_z_sym(t):
+                assert np.array_equal(o.sigma_of_t(t, ell), np.arange(ell ** 3))
+        assert {o.g_index(t) for t in T} == set(range(48))
+
+
+@pytest.mark.parametrize("ell,kind", [(3, 0), (4, 0), (5, 0), (4, 1), (4, 2)])
+def test_reflection_identity_all_316(ell, kind):
+    """K_t[a, b] = K_{p(t)}[sigma_t(a), sigma_t(b)] for every t (Eq. (25)).
+
+    The reverse orientation (sigma_t^{-1}) must fail exactly for the sigma
+    that are not involutions, which pins the reading of P_t.
+    """
+    c = 0.01 if kind == 2 else 0.0
+    level = 3
+    ops = o.operator_table(ell, kind, c, level)
+    lut = o.lut343()
+    tsym = o.t_sym_list()
+    n_fail_inverse = 0
+    n_non_involution = 0
+    for t in o.transfer_vectors():
+        s = o.t_slot(t)
+        p, g = int(lut[s]) & 0xFF, int(lut[s]) >> 8
+        assert tsym[p] == o.p_vector(t)
+        sig = o.sigma_of_t(t, ell)
+        Kp = ops[o.t_slot(tsym[p])]
+        Kt = ops[s]
+        rel = np.max(np.abs(Kp[np.ix_(sig, sig)] - Kt)) / np.max(np.abs(Kt))
+        assert rel < 4e-15
+        inv = np.argsort(sig)
+        if np.max(np.abs(Kp[np.ix_(inv, inv)] - Kt)) / np.max(np.abs(Kt)) > 1e-10:
+            n_fail_inverse += 1
+        if not np.array_equal(sig[sig], np.arange(ell ** 3)):
+            n_non_involution += 1
+    assert n_fail_inverse == n_non_involution > 0
+
+
+def test_lut_encoding():
+    lut = o.lut343()
+    for t in itertools.product(range(-3, 4), repeat=3):
+        v = int(lut[o.t_slot(t)])
+        if max(map(abs, t)) <= 1:
+            assert v == 0xFFFF
+        else:
+            assert (v & 0xFF) < 16 and (v >> 8) < 48
+
+
+def test_transpose_identity():
+    """K_{-t} = K_t^T: the kernel is symmetric, K(x, y) = K(y, x)."""
+    ops = o.operator_table(4, 0, 0.0, 3)
+    for t in o.transfer_vectors():
+        mt = tuple(-v for v in t)
+        A, B = ops[o.t_slot(t)], ops[o.t_slot(mt)]
+        assert np.max(np.abs(A - B.T)) <= 1e-15 * np.max(np.abs(A))
+
+
+@pytest.mark.parametrize("kind,n", [(0, -1), (1, -4)])
+def test_homogeneity_across_levels(kind, n):
+    """K(alpha r) = alpha^n K(r) (Sec. 3.2): halving the width scales K_t by 2^-n."""
+    assert o.homogeneity_degree(kind) == n
+    for t in [(2, 0, 0), (3, -1, 2), (-3, -3, -3)]:
+        K3 = o.operator_for_t(4, kind, 0.0, 3, t)
+        K4 = o.operator_for_t(4, kind, 0.0, 4, t)
+        assert np.allclose(K4, K3 * 2.0 ** (-n), rtol=1e-13, atol=0)
+
+
+def test_singular_values_invariant_under_reflection():
+    ops = o.operator_table(4, 0, 0.0, 2)
+    tsym = o.t_sym_list()
+    for t in o.transfer_vectors():
+        s1 = np.linalg.svd(ops[o.t_slot(t)], compute_uv=False)
+        s2 = np.linalg.svd(ops[o.t_slot(o.p_vector(t))], compute_uv=False)
+        assert np.allclose(s1, s2, rtol=1e-12, atol=1e-12 * s1[0])
+    assert len(tsym) == 16
+
+
+def test_eckart_young_truncation():
+    ops = o.operator_table(5, 1, 0.0, 3)
+    for t in [(2, 0, 0), (3, 1, -2), (-3, 3, 3)]:
+        K = ops[o.t_slot(t)]
+        s = np.linalg.svd(K, compute_uv=False)
+        for eps in (1e-3, 1e-6, 1e-9):
+            U, V, r = o.lowrank(K, eps)
+            assert s[r - 1] > eps * s[0]
+            if r < len(s):
+                assert s[r] <= eps * s[0]
+                err2 = np.linalg.norm(K - U @ V.T, 2)
+                assert abs(err2 - s[r]) <= 1e-9 * s[0]
+    assert o.truncation_rank(np.array([3.0, 2.0, 1.0]), 0.0) == 3
+
+
+# ---------------------------------------------------------------- kernels / direct sum
+def test_direct_sum_closed_form():
+    x = np.array([[0.0, 0.0, 0.0], [3.0, 4.0, 0.0]])
+    y = np.array([[0.0, 0.0, 0.0], [3.0, 0.0, 4.0]])
+    q = np.array([2.0, 5.0])
+    d01 = np.sqrt(9 + 16 + 0.0)   # x0 to y1
+    d10 = np.sqrt(0 + 16 + 16.0)  # x1 to y1
+    d11 = 5.0                     # x1 to y0
+    f = o.direct_sum(0, 0.0, x, y, q)
+    assert np.allclose(f, [5.0 / d01, 2.0 / d11 + 5.0 / d10], rtol=1e-15)
+    f = o.direct_sum(1, 0.0, x, y, q)
+    assert np.allclose(f, [5.0 / d01 ** 4, 2.0 / d11 ** 4 + 5.0 / d10 ** 4], rtol=1e-15)
+    f = o.direct_sum(2, 0.5, x, y, q)
+    # the coincident pair is skipped for every kernel, softened or not
+    assert np.allclose(f, [5.0 / np.sqrt(25 + 0.25),
+                           2.0 / np.sqrt(25.25) + 5.0 / np.sqrt(32.25)], rtol=1e-15)
+
+
+# ---------------------------------------------------------------- M2L apply
+def test_single_pair_interpolation_converges():
+    """P2M -> M2L (oracle K_t) -> L2P between two well-separated cells approaches
+    the direct sum (Eq. (5)); a transposed or mis-signed K_t would not."""
+    rng = np.random.default_rng(7)
+    level = 3
+    w = o.cell_width(level)
+    X, Y = np.array([3, 3, 3]), np.array([1, 4, 2])
+    t = tuple(int(v) for v in X - Y)
+    cx, cy = o.cell_center(X, level), o.cell_center(Y, level)
+    ys = cy + 0.5 * w * rng.uniform(-1, 1, (40, 3))
+    xs = cx + 0.5 * w * rng.uniform(-1, 1, (30, 3))
+    q = rng.standard_normal(40)
+    exact = o.direct_sum(0, 0.0, xs, ys, q)
+    errs = []
+    for ell in (2, 3, 4, 5, 6, 7):
+        W = o.interp_matrix(ell, ys, cy, w).T @ q
+        K = o.operator_for_t(ell, 0, 0.0, level, t)
+        F = K @ W
+        f = o.l2p(ell, xs, cx, w, F)
+        errs.append(o.rel_l2(f, exact))
+        Kwrong = o.operator_for_t(ell, 0, 0.0, level, tuple(-v for v in t))
+        if ell >= 4:
+            assert o.rel_l2(o.l2p(ell, xs, cx, w, Kwrong @ W), exact) > 100 * errs[-1]
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < 1e-5
+
+
+def test_fmm_converges_to_direct_sum():
+    """The whole FMM with oracle M2L at levels 2-3 vs the direct N^2 sum:
+    the error falls with ell (Sec. 5.1, roughly a decade per order)."""
+    rng = np.random.default_rng(2)
+    N = 1500
+    pts = rng.uniform(-1, 1, (N, 3))
+    q = rng.uniform(-1, 1, N)
+    samp = np.arange(0, N, 15)
+    exact = o.direct_sum(0, 0.0, pts[samp], pts, q)
+    errs = []
+    for ell in (2, 3, 4, 5):
+        up = o.UpwardPass(ell, 3, pts, q)
+        loc = o.fmm_oracle_locals(up, 0, 0.0)
+        errs.append(o.rel_l2(o.fmm_at_samples(up, 0, 0.0, loc, samp), exact))
+    assert all(b < 0.5 * a for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < 1e-4
+
+
+def test_adjoint_dot_product_identity():
+    rng = np.random.default_rng(4)
+    ell = 3
+    cells = o.full_grid_cells(3)
+    cells = cells[rng.random(len(cells)) < 0.7]
+    off, src = o.interaction_lists(cells, cells)
+    ops = o.operator_table(ell, 0, 0.0, 3)
+    w = rng.standard_normal((len(cells), ell ** 3))
+    g = rng.standard_normal((len(cells), ell ** 3))
+    Mw = o.m2l_apply(ops, cells, cells, off, src, w)
+    Mtg = o.m2l_apply_adjoint(ops, cells, cells, off, src, g, len(cells))
+    a, b = float(np.sum(g * Mw)), float(np.sum(Mtg * w))
+    assert abs(a - b) <= 1e-13 * (abs(a) + abs(b))
+
+
+def test_apply_matches_pairwise_assembly_tiny():
+    """Brute force on a tiny level: every pair assembled from its own cells' nodes."""
+    rng = np.random.default_rng(8)
+    ell, level = 2, 2
+    cells = o.full_grid_cells(level)
+    off, src = o.interaction_lists(cells, cells)
+    w = rng.standard_normal((len(cells), ell ** 3))
+    ops = o.operator_table(ell, 0, 0.0, level)
+    f = o.m2l_apply(ops, cells, cells, off, src, w)
+    wd = o.cell_width(level)
+    ref = np.zeros_like(f)
+    for x in range(len(cells)):
+        xn = o.cell_nodes(ell, o.cell_center(cells[x], level), wd)
+        for e in range(off[x], off[x + 1]):
+            y = src[e]
+            yn = o.cell_nodes(ell, o.cell_center(cells[y], level), wd)
+            D = np.linalg.norm(xn[:, None, :] - yn[None, :, :], axis=2)
+            ref[x] += (1.0 / D) @ w[y]
+    assert np.allclose(f, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+def test_apply_rejects_near_field_pair():
+    cells = np.array([[0, 0, 0], [1, 0, 0]], dtype=np.int32)
+    ops = o.operator_table(2, 0, 0.0, 2)
+    with pytest.raises(ValueError):
+        o.m2l_apply(ops, cells, cells, np.array([0, 1, 1], np.int32), np.array([1], np.int32),
+                    np.zeros((2, 8)))
+
+
+def test_rel_err_definition():
+    assert o.rel_l2([1.0, 2.0], [1.0, 2.0]) == 0.0
+    assert abs(o.rel_l2([0.0, 0.0], [3.0, 4.0]) - 1.0) < 1e-15
