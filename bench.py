@@ -1,0 +1,466 @@
+#!/usr/bin/env python
+"""Throughput of the symmetry-blocked M2L translation on one GB300.
+
+Workload (the symmetry-blocked FP64/FP32 configuration): a uniform octree of
+[-1,1]^3 holding N = 2,000,000 particles U([-1,1]^3) with leaf level 5, so
+levels 2..5 are full grids (64 .. 32768 cells, 6,039,504 far-field
+interactions in total); Chebyshev order ell = 5 (125 nodes), kernel 1/r.
+Multipole vectors are seeded N(0,1) stand-ins for the upward pass (the values
+do not change the work).
+
+One step = one pass of the whole hot path:
+  a1+a2  m2l_ops_rebuild      (16 operators and the permutation tables, on device)
+  a3     m2l_classify_level   (per level 2..5)
+  a4-a6  m2l_apply_classified (per level 2..5, the fused gather/GEMM/scatter kernel)
+value = far-field interactions of levels 2..5 / step time, summed over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ELL = 5
+LEVELS = (2, 3, 4, 5)
+KERNEL = 0  # 1/r
+N_PARTICLES = 2_000_000
+SEED = 2
+WORKLOAD = ("uniform octree of [-1,1]^3, N=2,000,000 particles U([-1,1]^3), leaf level 5 (levels 2-5 full: "
+            "64/512/4096/32768 cells), ell=5 (125 nodes), kernel 1/r, multipoles N(0,1) seed 2")
+METRIC = "M2L interactions/s (levels 2-5, one pass of the hot path)"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+NOMINAL = {"bf16": 2250.0, "tf32": 1100.0}
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FLOPS_PER_INTERACTION = 2 * (ELL ** 3) ** 2
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def full_interactions(level):
+    n = 1 << level
+    a = sum(1 for x in range(n) for y in range(n) if abs((x >> 1) - (y >> 1)) <= 1)
+    b = 3 * n - 2
+    return a ** 3 - b ** 3
+
+
+class ClockSampler:
+    """nvidia-smi clock samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_selector(device):
+    """nvidia-smi -i argument of the GPU torch runs on (its UUID when torch knows it)."""
+    import torch
+    props = torch.cuda.get_device_properties(device)
+    u = getattr(props, "uuid", None)
+    if u is not None:
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        return vis.split(",")[device.index or 0].strip()
+    return str(device.index or 0)
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value, device):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------------------------
+def cpu_oracle_sample(ntargets=2048, seed=11):
+    """The oracle, as it stands, on a bounded sample of the level-5 workload:
+    the 316 directly assembled operators plus the cell-by-cell M2L of
+    `ntargets` random level-5 target cells with their full lists."""
+    import numpy as np
+
+    import oracle
+    from paper_1210_7292_gb300 import synth
+    cells = synth.full_grid(5)
+    w = synth.gaussian_vectors(len(cells), ELL ** 3, seed=SEED)
+    rng = np.random.default_rng(seed)
+    samp = np.sort(rng.choice(len(cells), ntargets, replace=False))
+    off, src = oracle.interaction_lists(cells[samp], cells)
+    t0 = time.perf_counter()
+    ops = oracle.operator_table(ELL, KERNEL, 0.0, 5)
+    oracle.m2l_apply(ops, cells[samp], cells, off, src, w)
+    dt = time.perf_counter() - t0
+    nint = int(off[-1])
+    return {"value": nint / dt, "unit": "interactions/s", "cores": 1, "kind": "oracle",
+            "sample": "%d random level-5 target cells (%d interactions) of the workload, 316 operators "
+                      "assembled directly, single-threaded C loops, %.1f s" % (ntargets, nint, dt),
+            "gflops": nint * FLOPS_PER_INTERACTION / dt / 1e9}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle  # noqa: F401  (built by build(); compiled here if missing)
+    oracle.build_c()
+    ntg = 256
+    for _ in range(args.warmup):
+        cpu_oracle_sample(ntargets=64)
+    vals, times = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = cpu_oracle_sample(ntargets=ntg)
+        times.append(time.perf_counter() - t0)
+        vals.append(r["value"])
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "fp64 (CPU oracle)", "l2_policy": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": 1, "kind": "oracle",
+                             "sample": "per step: %d random level-5 target cells with full lists, 316 directly "
+                                       "assembled operators, single-threaded C loops" % ntg},
+            "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------------------------
+class Workload:
+    def __init__(self, m2l, device, precision, seed):
+        import numpy as np
+        import torch
+
+        from paper_1210_7292_gb300 import synth
+        self.m2l, self.device, self.precision = m2l, device, precision
+        self.ops = m2l.m2l_precompute(m2l.M2L_K_INV_R, ELL)
+        self.dt_in = torch.float64 if precision == "fp64" else torch.float32
+        self.levels, self.mp, self.loc = {}, {}, {}
+        self.host = {}
+        self.nint = {}
+        for L in LEVELS:
+            cells = synth.full_grid(L)
+            ijk = torch.from_numpy(cells).to(device)
+            off, src = m2l.m2l_build_lists(ijk, ijk)
+            self.levels[L] = m2l.Level(2.0 / (1 << L), ijk, ijk, off, src, L)
+            w = synth.gaussian_vectors(len(cells), ELL ** 3, seed=seed + 100 * L)
+            self.mp[L] = torch.from_numpy(w).to(device, self.dt_in)
+            self.loc[L] = torch.zeros(len(cells), ELL ** 3, dtype=self.dt_in, device=device)
+            self.nint[L] = self.levels[L].nnz
+            # pinned host copies for the end-to-end leg
+            self.host[L] = {"mp": torch.from_numpy(w).to(self.dt_in).pin_memory(),
+                            "ijk": torch.from_numpy(cells).pin_memory(),
+                            "off": off.cpu().pin_memory(), "src": src.cpu().pin_memory(),
+                            "loc": torch.zeros(len(cells), ELL ** 3, dtype=self.dt_in).pin_memory()}
+        self.total = sum(self.nint.values())
+        assert self.nint[5] == full_interactions(5)
+
+    def step(self, kev=None):
+        m2l = self.m2l
+        m2l.m2l_ops_rebuild(self.ops)
+        for L in LEVELS:
+            m2l.m2l_classify_level(self.ops, self.levels[L])
+            if kev is not None:
+                kev[L][0].record()
+            m2l.m2l_apply_classified(self.ops, self.mp[L], self.loc[L], self.precision)
+            if kev is not None:
+                kev[L][1].record()
+
+    def e2e_step(self):
+        """Same step through the public API from pinned host buffers: inputs copied in,
+        locals copied out, inside the timed region."""
+        import torch
+        m2l = self.m2l
+        dev_lv = {}
+        for L in LEVELS:
+            h = self.host[L]
+            ijk = h["ijk"].to(self.device, non_blocking=True)
+            off = h["off"].to(self.device, non_blocking=True)
+            src = h["src"].to(self.device, non_blocking=True)
+            mp = h["mp"].to(self.device, non_blocking=True)
+            dev_lv[L] = (m2l.Level(2.0 / (1 << L), ijk, ijk, off, src, L), mp)
+        m2l.m2l_ops_rebuild(self.ops)
+        for L in LEVELS:
+            lv, mp = dev_lv[L]
+            loc = torch.zeros(lv.struct.ncells_tgt, ELL ** 3, dtype=self.dt_in, device=self.device)
+            m2l.m2l_apply_level(self.ops, lv, mp, loc, self.precision)
+            self.host[L]["loc"].copy_(loc, non_blocking=True)
+        return dev_lv
+
+    def e2e_bytes(self):
+        h2d = d2h = 0
+        for L in LEVELS:
+            h = self.host[L]
+            h2d += sum(t.numel() * t.element_size() for t in (h["mp"], h["ijk"], h["off"], h["src"]))
+            d2h += h["loc"].numel() * h["loc"].element_size()
+        return h2d, d2h
+
+
+def timed(fn, steps, flush, device, kernel_events=False, levels=LEVELS):
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    kev = [{L: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for L in levels}
+           for _ in range(steps)] if kernel_events else None
+    for i in range(steps):
+        flush.zero_()   # evict L2 between timed steps (outside the event pair)
+        evs[i][0].record()
+        if kernel_events:
+            fn(kev[i])
+        else:
+            fn()
+        evs[i][1].record()
+    torch.cuda.synchronize(device)
+    total = sum(s.elapsed_time(e) for s, e in evs) / 1e3
+    kt = None
+    if kernel_events:
+        kt = {L: [k[L][0].elapsed_time(k[L][1]) / 1e3 for k in kev] for L in levels}
+    return total, kt
+
+
+def traffic_for(kernel_name):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    ent = d.get(kernel_name)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_1210_7292_gb300", "csrc", ent["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] if os.path.exists(src) else None
+    return ent["dram_bytes_per_launch"] if h == ent.get("source_sha256_16") else None
+
+
+KERNEL_FOR = {"fp64": ("simt_apply_kernel<double>", "m2l_apply_simt.cu", "alu"),
+              "fp32": ("simt_apply_kernel<float>", "m2l_apply_simt.cu", "alu"),
+              "tf32": ("tc_apply_kernel<tf32>", "m2l_apply_tc.cu", "tensor"),
+              "bf16x3": ("tc_apply_kernel<bf16x3>", "m2l_apply_tc.cu", "tensor"),
+              "tf32x3": ("tc_apply_kernel<tf32x3>", "m2l_apply_tc.cu", "tensor")}
+
+
+def roofline(precision, achieved_tflops, peaks, src_kind):
+    kname, src, bound = KERNEL_FOR[precision]
+    if precision == "fp32":
+        peak, how = FP32_ALU_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
+    elif precision == "fp64":
+        peak, how = 1.25, "nominal FP64 1.25 TFLOP/s (no measured FP64 peak in MEASURED_PEAKS)"
+    else:
+        bf = peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"])
+        if precision == "tf32":
+            peak, how = bf * NOMINAL["tf32"] / NOMINAL["bf16"], "bf16 sustained (%s) x 1.1/2.25" % src_kind
+        elif precision == "bf16x3":
+            peak, how = bf / 3.0, "bf16 sustained (%s) / 3 products" % src_kind
+        else:
+            peak, how = bf * NOMINAL["tf32"] / NOMINAL["bf16"] / 3.0, "bf16 sustained (%s) x 1.1/2.25 / 3" % src_kind
+    return {"bound": bound, "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved_tflops / peak, "traffic": traffic_for(kname), "kernel": kname, "peak_source": how,
+            "flops_per_launch": FLOPS_PER_INTERACTION * full_interactions(5),
+            "flop_convention": "algorithmic 2*ell^6 per interaction, level-5 launch"}
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a GPU (the product path has no CPU fallback)")
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    import __graft_entry__ as g
+    g.build()
+    from paper_1210_7292_gb300 import m2l
+    prec = args.precision
+    wl = Workload(m2l, device, prec, SEED + rank)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+    for _ in range(args.warmup):
+        wl.step()
+    torch.cuda.synchronize(device)
+    m2l.m2l_sync_status(wl.ops)
+    clocks = ClockSampler(gpu_selector(device))
+    barrier(world)
+    torch.cuda.synchronize(device)
+    launches0 = m2l.m2l_launch_count()
+    clocks.start()
+    total, kt = timed(wl.step, args.steps, flush, device, kernel_events=True)
+    clk = clocks.stop()
+    launches = m2l.m2l_launch_count() - launches0
+    torch.cuda.synchronize(device)
+    barrier(world)
+    m2l.m2l_sync_status(wl.ops)
+    tmax = max_over_ranks(world, total, device)
+    value = world * wl.total * args.steps / tmax
+    k5 = statistics.mean(kt[5])
+    ach = FLOPS_PER_INTERACTION * wl.nint[5] / k5 / 1e12
+    peaks, src_kind = measured_peaks()
+
+    # end-to-end leg through host buffers
+    for _ in range(2):
+        wl.e2e_step()
+    torch.cuda.synchronize(device)
+    barrier(world)
+    e2e_total, _ = timed(wl.e2e_step, max(2, args.steps // 2), flush, device)
+    e2e_max = max_over_ranks(world, e2e_total, device)
+    e2e_val = world * wl.total * max(2, args.steps // 2) / e2e_max
+    h2d, d2h = wl.e2e_bytes()
+
+    # FP64 and the other precisions beside the headline, with their error vs FP64 at level 5
+    extra = {}
+    if rank == 0 and not args.quick:
+        ref64 = None
+        for p in ["fp64"] + [q for q in args.compare if q != "fp64"]:
+            try:
+                w2 = wl if p == prec else Workload(m2l, device, p, SEED)
+                for _ in range(1):
+                    w2.step()
+                torch.cuda.synchronize(device)
+                for L in LEVELS:
+                    w2.loc[L].zero_()
+                t2, kt2 = timed(w2.step, 2 if p == "fp64" else 5, flush, device, kernel_events=True)
+                res = {"interactions_per_s": w2.total * (2 if p == "fp64" else 5) / t2,
+                       "level5_kernel_ms": 1e3 * statistics.mean(kt2[5]),
+                       "level5_gflops": FLOPS_PER_INTERACTION * w2.nint[5] / statistics.mean(kt2[5]) / 1e9}
+                loc5 = w2.loc[5].double() / (2 if p == "fp64" else 5)
+                if p == "fp64":
+                    ref64 = loc5
+                    res["rel_l2_vs_fp64"] = 0.0
+                elif ref64 is not None:
+                    res["rel_l2_vs_fp64"] = float(torch.linalg.norm(loc5 - ref64) / torch.linalg.norm(ref64))
+                extra[p] = res
+            except m2l.M2LError as e:
+                extra[p] = {"unavailable": str(e)}
+    cpu = cpu_oracle_sample() if (rank == 0 and world == 1 and not args.quick) else None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64"}.get(prec, "f32"),
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "precision": prec, "levels": list(LEVELS),
+                           "interactions_per_step_per_gpu": wl.total,
+                           "l2_policy": "inputs (49 MB) fit in L2: a 256 MB buffer is written between timed steps",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "gflops": value * FLOPS_PER_INTERACTION / 1e9,
+                "level5_kernel_ms": 1e3 * k5,
+                "roofline": roofline(prec, ach, peaks, src_kind),
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e_val, "unit": "interactions/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches,
+                "clocks": clk,
+                "precisions": extra}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32", "bf16x3", "tf32x3"])
+    ap.add_argument("--compare", default="fp32", help="comma list of extra precisions to report")
+    ap.add_argument("--quick", action="store_true", help="skip the extra precisions and the CPU baseline")
+    args = ap.parse_args()
+    args.compare = [p for p in args.compare.split(",") if p]
+    if args.warmup < 3:
+        log("warmup raised to 3")
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

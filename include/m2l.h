@@ -1,0 +1,236 @@
+/*
+ * m2l.h -- C ABI of the GB300 (sm_103a) M2L library.
+ *
+ * The library computes the multipole-to-local (M2L) translation of the
+ * black-box Chebyshev fast multipole method for one octree level at a time,
+ * following Messner, Bramas, Coulaud and Darve, "Optimized M2L kernels for
+ * the Chebyshev interpolation based fast multipole method":
+ *
+ *   F_alpha = sum_beta K(xbar_alpha, ybar_beta) W_beta            (Eq. (7))
+ *
+ * for every far-field pair (X, Y) of the level.  The 316 operators K_t of a
+ * level (Eq. (15)) are expressed as permutations of 16 unique ones
+ * (Eq. (25), Sec. 4.2.1); interactions sharing an operator are blocked into
+ * matrix-matrix products (Alg. 2, Sec. 4.2.3), optionally on per-operator
+ * SVD-compressed factors (Eq. (20), Sec. 4.2).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named "device" are CUDA device pointers owned by the caller;
+ *    "host" pointers are ordinary host memory owned by the caller.  The
+ *    library owns m2l_ops and m2l_plan objects and the workspace inside them.
+ *  - Streams are cudaStream_t values passed as void* (NULL = legacy default
+ *    stream).  Every device operation is stream-ordered on that stream; apply
+ *    calls return before the GPU has finished.
+ *  - Node vectors (multipoles W, locals F) are row-major [ncells][ell^3];
+ *    within a vector, node alpha = (a1, a2, a3) (zero-based) sits at
+ *    m(alpha) = a1 + a2*ell + a3*ell^2 (Eq. (16), x fastest).
+ *  - Chebyshev nodes on the reference interval are the roots of T_ell in
+ *    ascending order, -cos((2k+1) pi / (2 ell)), k = 0..ell-1 (Sec. 2.1).
+ *  - The transfer vector of a pair is t = X - Y (target minus source) in
+ *    integer cell coordinates (Sec. 3.1).  Every list entry must satisfy
+ *    |t|_inf in {2, 3}.
+ *  - No exception crosses the ABI: every entry point returns an m2l_status;
+ *    m2l_last_error() gives a message for the calling thread.  Errors found
+ *    by a kernel (a list entry that is not a far-field pair, an index out of
+ *    range, a wait that timed out) set a status word on the device; the
+ *    entries concerned are skipped and m2l_sync_status() reports the error.
+ */
+#ifndef M2L_H
+#define M2L_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    M2L_OK = 0,
+    M2L_EINVAL = 1,        /* bad argument, or a bad interaction list found on the device */
+    M2L_ENOMEM = 2,        /* a device allocation failed */
+    M2L_ECUDA = 3,         /* a CUDA runtime or library call failed */
+    M2L_ETIMEOUT = 4,      /* a bounded device wait gave up (kernel returned early) */
+    M2L_EUNSUPPORTED = 5   /* valid request this build cannot serve (e.g. order too large) */
+} m2l_status;
+
+/* Kernel functions (Sec. 1; Eq. (33) with the 4*pi factor dropped). */
+typedef enum {
+    M2L_K_INV_R = 0,          /* 1/r, homogeneous of degree -1 */
+    M2L_K_INV_R4 = 1,         /* 1/r^4, homogeneous of degree -4 */
+    M2L_K_INV_SQRT_R2C2 = 2   /* 1/sqrt(r^2 + c^2), not homogeneous */
+} m2l_kernel_type;
+
+typedef struct {
+    int type;   /* m2l_kernel_type */
+    double c;   /* used by M2L_K_INV_SQRT_R2C2 only */
+} m2l_kernel;
+
+/* Arithmetic of the operator products (step 2 of Sec. 4.2.2).
+ * Multipoles are double for M2L_FP64 and float otherwise. */
+typedef enum {
+    M2L_FP64 = 0,    /* FP64 SIMT products, FP64 accumulation */
+    M2L_FP32 = 1,    /* FP32 SIMT products, FP32 accumulation */
+    M2L_TF32 = 2,    /* tcgen05 kind::tf32 tensor-core products, FP32 accumulation in TMEM */
+    M2L_BF16X3 = 3,  /* tcgen05 kind::f16 with bf16 hi/lo splits, three products
+                        (hi*hi + hi*lo + lo*hi), FP32 accumulation in TMEM */
+    M2L_TF32X3 = 4   /* tcgen05 kind::tf32 with tf32 hi/lo splits, three products */
+} m2l_precision;
+
+typedef struct m2l_ops m2l_ops;    /* opaque, library-owned */
+typedef struct m2l_plan m2l_plan;  /* opaque, library-owned */
+
+/* One octree level's interaction lists.  All pointers are device pointers
+ * owned by the caller and must stay valid until the work that uses them has
+ * run on the stream. */
+typedef struct {
+    int level;                   /* octree level, informational */
+    double width;                /* cell width w of this level (> 0) */
+    int ncells_tgt;              /* number of target cells (>= 0, < 2^26) */
+    int ncells_src;              /* number of source cells (>= 0, < 2^26) */
+    const int32_t *tgt_ijk;      /* device [ncells_tgt][3] integer coordinates of the targets */
+    const int32_t *src_ijk;      /* device [ncells_src][3] integer coordinates of the sources */
+    const int32_t *il_offsets;   /* device [ncells_tgt + 1] CSR row offsets over targets, il_offsets[0] = 0 */
+    const int32_t *il_sources;   /* device [nnz] source indices in [0, ncells_src) */
+    int nnz;                     /* number of list entries, equal to il_offsets[ncells_tgt] */
+} m2l_level;
+
+/* ---------------------------------------------------------------------
+ * Precompute (Sec. 4.2.1 and Sec. 4.2): builds, on the current device,
+ *  - the 16 unique operators K_p, t_p in T_sym = {t1 >= t2 >= t3 >= 0}
+ *    (Eqs. (23)-(24)), in FP64, K_p[m(alpha)][n(beta)] = K(xbar_alpha, ybar_beta)
+ *    (Eq. (15)).  Homogeneous kernels are assembled at unit width and scaled
+ *    by w^degree at apply time (Sec. 3.2); 1/sqrt(r^2+c^2) is assembled at
+ *    `width` and may only be applied to levels of that width;
+ *  - the 48 permutation tables sigma_g (Eqs. (26)-(29)) and the 343-entry
+ *    table t -> (p, g);
+ *  - when eps > 0, a truncated SVD of each K_p, K_p ~ (U_p Sigma_p) V_p^T
+ *    (Eq. (20)), at the smallest rank r_p with s_{r+1} <= eps * s_1.
+ * ell: Chebyshev order, 2 <= ell <= 8.  eps: 0 for full rank, else in (0, 1).
+ * width: cell width for the non-homogeneous kernel (ignored otherwise).
+ * out: receives a new m2l_ops; free with m2l_ops_free.
+ * Synchronous (returns after the device work is done).  Errors: M2L_EINVAL
+ * for out-of-range arguments, M2L_ENOMEM, M2L_ECUDA. */
+m2l_status m2l_precompute(m2l_kernel kernel, int ell, double eps, double width, m2l_ops **out);
+
+/* Re-runs the device assembly of the full-rank operators and tables of
+ * `ops` into its existing buffers (no allocation), stream-ordered.  Used to
+ * time the precompute as part of a step.  M2L_EUNSUPPORTED for ops built with
+ * eps > 0. */
+m2l_status m2l_ops_rebuild(m2l_ops *ops, void *stream);
+
+/* Host copies of the tables, for checking (Sec. 4.2.1).  Any output may be
+ * NULL.  ranks16: [16] ranks r_p (ell^3 when full rank).  sigma48: [48][ell^3]
+ * with sigma48[g][j] = m(pi_g(m^{-1}(j))), g = 8 * perm_id + flip_mask where
+ * flip_mask bit i is set when t_i < 0 and perm_id indexes the axis order
+ * (|t_i| >= |t_j| >= |t_k|, ties by lower axis first) among the six
+ * permutations of (0,1,2) in lexicographic order.  lut343: at slot
+ * (t1+3) + 7 (t2+3) + 49 (t3+3), p | (g << 8), with p the index of p(t) in
+ * T_sym sorted lexicographically ascending, or 0xFFFF for |t|_inf <= 1.
+ * Then K_t[a][b] = K_p[sigma_g(a)][sigma_g(b)]. */
+m2l_status m2l_ops_query(const m2l_ops *ops, int *ranks16, int16_t *sigma48, uint16_t *lut343);
+
+/* Host copy of the 16 FP64 operators as stored ([16][ell^3][ell^3], at unit
+ * width for homogeneous kernels).  host_out must hold 16 * ell^6 doubles. */
+m2l_status m2l_ops_copy_operators(const m2l_ops *ops, double *host_out);
+
+/* Host copy of the low-rank factors of operator p: U (= U_p Sigma_p) and V,
+ * both [ell^3][r_p] row-major.  M2L_EINVAL when ops is full rank. */
+m2l_status m2l_ops_copy_lowrank(const m2l_ops *ops, int p, double *host_U, double *host_V);
+
+/* Basic facts of an ops object; any output may be NULL. */
+m2l_status m2l_ops_info(const m2l_ops *ops, int *ell, int *kernel_type, double *eps,
+                        double *ref_width, int *homogeneity_degree);
+
+void m2l_ops_free(m2l_ops *ops);
+
+/* ---------------------------------------------------------------------
+ * Apply (Eq. (7) through Eqs. (30)-(32) and Alg. 2):
+ *   locals[X] += sum_{Y in list(X)} K_{t(X,Y)} multipoles[Y]
+ * Step a3: every entry is classified by t -> (p, g) and bucketed per
+ * operator p, ordered by target (stable).  Steps a4-a6 run in one fused
+ * kernel per precision: gather and permute the source vectors into the
+ * panel W_p (W_p[sigma_g(b)] = w[b]), product F_p = K_p W_p, un-permute
+ * (f[a] += F_p[sigma_g(a)]), sum over the columns of one target, scaled by
+ * w^degree for homogeneous kernels, and one atomic add per target and node.
+ * multipoles: device [ncells_src][ell^3], double for M2L_FP64 else float.
+ * locals:     device [ncells_tgt][ell^3], accumulated (+=); double when
+ *             precision == M2L_FP64 or locals_fp64 != 0, else float.
+ * The workspace of ops is used: two apply calls on one ops object must not
+ * overlap on the GPU (use plans, below, for that).
+ * Errors: M2L_EINVAL (bad sizes, mismatched width for the non-homogeneous
+ * kernel), M2L_EUNSUPPORTED, M2L_ENOMEM, M2L_ECUDA; list errors found on the
+ * device are reported by m2l_sync_status. */
+m2l_status m2l_apply_level(const m2l_ops *ops, const m2l_level *level, const void *multipoles,
+                           void *locals, int precision, int locals_fp64, void *stream);
+
+/* Adjoint of m2l_apply_level: grad_multipoles[Y] += K_t^T grad_locals[X]
+ * over the same pairs.  Since K_{-t} = K_t^T (the kernel is symmetric), this
+ * is the forward translation on the transposed list, which the library
+ * builds on the device.  grad_locals: [ncells_tgt][ell^3];
+ * grad_multipoles: [ncells_src][ell^3], accumulated; types as for apply with
+ * the roles of the two arrays exchanged. */
+m2l_status m2l_apply_level_adjoint(const m2l_ops *ops, const m2l_level *level,
+                                   const void *grad_locals, void *grad_multipoles,
+                                   int precision, int grad_fp64, void *stream);
+
+/* The two halves of m2l_apply_level, for callers that time or overlap them:
+ * m2l_classify_level runs step a3 into the workspace of ops (growing it on
+ * first use), m2l_apply_classified runs steps a4-a6 on the last
+ * classification of ops (same argument meanings as m2l_apply_level; the
+ * level's width is remembered).  Both are stream-ordered; the pair on one ops
+ * object must not overlap another apply on that object. */
+m2l_status m2l_classify_level(const m2l_ops *ops, const m2l_level *level, void *stream);
+m2l_status m2l_apply_classified(const m2l_ops *ops, const void *multipoles, void *locals, int precision,
+                                int locals_fp64, void *stream);
+
+/* Plans: the classification (step a3) of one level's lists, kept in
+ * plan-owned device memory so that repeated applies on unchanged lists skip
+ * it.  The level's ijk/list arrays are read at creation only.  adjoint != 0
+ * plans the transposed translation.  m2l_plan_apply allocates nothing and is
+ * stream-ordered. */
+m2l_status m2l_plan_create(const m2l_ops *ops, const m2l_level *level, int adjoint, void *stream,
+                           m2l_plan **out);
+m2l_status m2l_plan_apply(const m2l_plan *plan, const void *in_vectors, void *out_vectors,
+                          int precision, int out_fp64, void *stream);
+/* Host copy of a plan's per-operator counts n_p ([16]) and bucketed records
+ * ([nvalid][3]: source index, target index, g, in execution order). */
+m2l_status m2l_plan_query(const m2l_plan *plan, int64_t *counts16, int32_t *records, int64_t *nvalid);
+void m2l_plan_free(m2l_plan *plan);
+
+/* Batched apply: nbatch independent (ops, level) problems in one persistent
+ * launch per precision family.  All ops must share one ell; in[i], out[i]
+ * follow the types of m2l_apply_level.  Classification runs per problem. */
+m2l_status m2l_apply_batch(const m2l_ops *const *ops, const m2l_level *levels,
+                           const void *const *multipoles, void *const *locals, int nbatch,
+                           int precision, int locals_fp64, void *stream);
+
+/* ---------------------------------------------------------------------
+ * Interaction lists (Sec. 3.2, Alg. 1 for asymptotically smooth kernels):
+ * Y is in the list of X when their parents are neighbours,
+ * |floor(X/2) - floor(Y/2)|_inf <= 1, and |X - Y|_inf >= 2.  Sources of a
+ * target are listed in ascending source index.  Two calls: with
+ * il_sources == NULL, writes the row offsets (device [ncells_tgt + 1]) and
+ * *nnz_out (host); then, with il_sources (device [nnz]), fills the lists.
+ * Cells are looked up in a dense table of side 2^max_coord_bits (<= 256).
+ * Synchronous. */
+m2l_status m2l_build_lists(int ncells_tgt, const int32_t *tgt_ijk, int ncells_src,
+                           const int32_t *src_ijk, int32_t *il_offsets, int32_t *il_sources,
+                           int64_t *nnz_out, void *stream);
+
+/* ---------------------------------------------------------------------
+ * Synchronises `stream`, then returns and clears the device status word of
+ * ops (M2L_OK, M2L_EINVAL for list entries that were skipped, M2L_ETIMEOUT). */
+m2l_status m2l_sync_status(const m2l_ops *ops, void *stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *m2l_last_error(void);
+
+/* Number of kernel launches the library has issued on this process (all
+ * entry points), for launch accounting. */
+int64_t m2l_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* M2L_H */

@@ -1,0 +1,315 @@
+// Step a3: classification of every interaction by its transfer vector and
+// stable bucketing per unique operator (the first loop of Alg. 2, blocked
+// along many target cells as in Sec. 4.2.3, "Blocking along multiple target
+// cells").
+//
+// For list entry e = (X, Y): t = X - Y (Sec. 3.1), (p, g) = lut(t).  Entries
+// are counting-sorted by p, keeping list order inside a bucket, so that each
+// bucket is ordered by target and the epilogue can sum the columns of one
+// target before its atomic add.  Output record: {Y, X | g << 26}.
+#include "m2l_internal.cuh"
+
+namespace m2l {
+namespace {
+
+constexpr int kScanThreads = 1024;
+
+// Target of every list entry; validates the CSR offsets.
+__global__ void tgt_of_kernel(int ntgt, int nnz, const int32_t *__restrict__ offsets,
+                              int32_t *__restrict__ tgt_of, int *__restrict__ status)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= ntgt) return;
+    const int o0 = offsets[warp], o1 = offsets[warp + 1];
+    bool ok = (o0 >= 0) && (o1 >= o0) && (o1 <= nnz);
+    if (warp == 0 && o0 != 0) ok = false;
+    if (warp == ntgt - 1 && o1 != nnz) ok = false;
+    if (!ok) {
+        if (lane == 0) atomicOr(status, ST_BAD_INDEX);
+        return;
+    }
+    for (int e = o0 + lane; e < o1; e += 32) tgt_of[e] = warp;
+}
+
+__device__ __forceinline__ uint16_t classify_entry(int e, const int32_t *__restrict__ tgt_of,
+                                                   const int32_t *__restrict__ sources,
+                                                   const int32_t *__restrict__ tgt_ijk,
+                                                   const int32_t *__restrict__ src_ijk, int nsrc,
+                                                   const uint16_t *__restrict__ lut, int *status)
+{
+    const int x = tgt_of[e];
+    const int y = sources[e];
+    if (x < 0 || y < 0 || y >= nsrc) {
+        atomicOr(status, ST_BAD_INDEX);
+        return 0xFFFF;
+    }
+    const int t0 = tgt_ijk[3 * x] - src_ijk[3 * y];
+    const int t1 = tgt_ijk[3 * x + 1] - src_ijk[3 * y + 1];
+    const int t2 = tgt_ijk[3 * x + 2] - src_ijk[3 * y + 2];
+    if (abs(t0) > 3 || abs(t1) > 3 || abs(t2) > 3) {
+        atomicOr(status, ST_BAD_PAIR);
+        return 0xFFFF;
+    }
+    const uint16_t c = lut[(t0 + 3) + 7 * (t1 + 3) + 49 * (t2 + 3)];
+    if (c == 0xFFFF) atomicOr(status, ST_BAD_PAIR);
+    return c;
+}
+
+// One warp per segment of kSegEntries entries: class codes and per-class counts.
+__global__ void code_count_kernel(int nnz, int nseg, const int32_t *__restrict__ tgt_of,
+                                  const int32_t *__restrict__ sources, const int32_t *__restrict__ tgt_ijk,
+                                  const int32_t *__restrict__ src_ijk, int nsrc,
+                                  const uint16_t *__restrict__ lut, uint16_t *__restrict__ code,
+                                  int32_t *__restrict__ seg_counts, int *__restrict__ status)
+{
+    __shared__ int cnt[4][17];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int seg = blockIdx.x * 4 + wib;
+    for (int i = lane; i < 17; i += 32) cnt[wib][i] = 0;
+    __syncwarp();
+    if (seg >= nseg) return;
+    const int e0 = seg * kSegEntries;
+    const int e1 = min(nnz, e0 + kSegEntries);
+    for (int base = e0; base < e1; base += 32) {
+        const int e = base + lane;
+        int cls = 17;
+        if (e < e1) {
+            const uint16_t c = classify_entry(e, tgt_of, sources, tgt_ijk, src_ijk, nsrc, lut, status);
+            code[e] = c;
+            cls = (c == 0xFFFF) ? 16 : (c & 0xFF);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, cls);
+        if (cls < 17 && lane == __ffs(peers) - 1) cnt[wib][cls] += __popc(peers);
+        __syncwarp();
+    }
+    for (int i = lane; i < 17; i += 32) seg_counts[(size_t)i * nseg + seg] = cnt[wib][i];
+}
+
+// Single-block exclusive scan of n ints; out[n] = total.
+__global__ void exclusive_scan_kernel(const int32_t *__restrict__ in, int32_t *__restrict__ out, int n)
+{
+    __shared__ int warp_sums[kScanThreads / 32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int base = 0; base < n; base += kScanThreads) {
+        const int i = base + threadIdx.x;
+        const int v = (i < n) ? in[i] : 0;
+        int incl = v;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += u;
+        }
+        if (lane == 31) warp_sums[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int s = warp_sums[lane];
+            for (int d = 1; d < 32; d <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, s, d);
+                if (lane >= d) s += u;
+            }
+            warp_sums[lane] = s;  // inclusive over warps
+        }
+        __syncthreads();
+        const int before = carry + (wid > 0 ? warp_sums[wid - 1] : 0);
+        if (i < n) out[i] = before + incl - v;
+        __syncthreads();
+        if (threadIdx.x == kScanThreads - 1) carry = before + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
+__global__ void class_offsets_kernel(int nseg, int nnz, const int32_t *__restrict__ pos,
+                                     int32_t *__restrict__ class_off)
+{
+    const int c = threadIdx.x;
+    if (c < 17) class_off[c] = pos[(size_t)c * nseg];
+    if (c == 17) class_off[17] = nnz;
+}
+
+// One warp per segment, in order: stable positions inside each bucket.
+__global__ void scatter_kernel(int nnz, int nseg, const uint16_t *__restrict__ code,
+                               const int32_t *__restrict__ tgt_of, const int32_t *__restrict__ sources,
+                               const int32_t *__restrict__ seg_pos, int2 *__restrict__ rec)
+{
+    __shared__ int base[4][17];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int seg = blockIdx.x * 4 + wib;
+    if (seg >= nseg) return;
+    for (int i = lane; i < 17; i += 32) base[wib][i] = seg_pos[(size_t)i * nseg + seg];
+    __syncwarp();
+    const int e0 = seg * kSegEntries;
+    const int e1 = min(nnz, e0 + kSegEntries);
+    const unsigned lt = (1u << lane) - 1u;
+    for (int b = e0; b < e1; b += 32) {
+        const int e = b + lane;
+        int cls = 17;
+        uint16_t c = 0xFFFF;
+        if (e < e1) {
+            c = code[e];
+            cls = (c == 0xFFFF) ? 16 : (c & 0xFF);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, cls);
+        int pos = 0;
+        if (cls < 17) pos = base[wib][cls] + __popc(peers & lt);
+        __syncwarp();
+        if (cls < 17 && lane == __ffs(peers) - 1) base[wib][cls] += __popc(peers);
+        __syncwarp();
+        if (cls < 16) rec[pos] = make_int2(sources[e], rec_pack(tgt_of[e], (int)(c >> 8)));
+    }
+}
+
+// ---- list transposition for the adjoint ----
+__global__ void count_sources_kernel(int nnz, int nsrc, const int32_t *__restrict__ tgt_of,
+                                     const int32_t *__restrict__ sources, int32_t *__restrict__ cnt,
+                                     int *__restrict__ status)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += gridDim.x * blockDim.x) {
+        const int y = sources[e];
+        if (y < 0 || y >= nsrc || tgt_of[e] < 0) {
+            atomicOr(status, ST_BAD_INDEX);
+            continue;
+        }
+        atomicAdd(cnt + y, 1);
+    }
+}
+
+__global__ void fill_transposed_kernel(int nnz, int nsrc, const int32_t *__restrict__ tgt_of,
+                                       const int32_t *__restrict__ sources, int32_t *__restrict__ cursor,
+                                       int32_t *__restrict__ t_src)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += gridDim.x * blockDim.x) {
+        const int y = sources[e];
+        const int x = tgt_of[e];
+        if (y < 0 || y >= nsrc || x < 0) continue;
+        const int pos = atomicAdd(cursor + y, 1);
+        t_src[pos] = x;
+    }
+}
+
+// One warp per transposed row: sort ascending by rank counting, so the
+// transposed list is independent of the atomic fill order.
+__global__ void sort_rows_kernel(int nrows, const int32_t *__restrict__ off, int32_t *__restrict__ vals,
+                                 int32_t *__restrict__ scratch)
+{
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= nrows) return;
+    const int o0 = off[row], o1 = off[row + 1];
+    for (int i = o0 + lane; i < o1; i += 32) {
+        const int v = vals[i];
+        int r = 0;
+        for (int j = o0; j < o1; ++j) {
+            const int u = vals[j];
+            r += (u < v) || (u == v && j < i);
+        }
+        scratch[o0 + r] = v;
+    }
+    __syncwarp();
+    for (int i = o0 + lane; i < o1; i += 32) vals[i] = scratch[i];
+}
+
+}  // namespace
+
+m2l_status launch_exclusive_scan(const int32_t *in, int32_t *out, int n, cudaStream_t s)
+{
+    exclusive_scan_kernel<<<1, kScanThreads, 0, s>>>(in, out, n);
+    M2L_LAUNCH_CHECK("exclusive_scan_kernel");
+    return M2L_OK;
+}
+
+static m2l_status bucket(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const int32_t *tgt_ijk,
+                         const int32_t *src_ijk, const int32_t *offsets, const int32_t *sources, Buckets &b,
+                         cudaStream_t s)
+{
+    m2l_status st;
+    const int nseg = (nnz + kSegEntries - 1) / kSegEntries;
+    if ((st = b.rec.ensure((size_t)(nnz > 0 ? nnz : 1) * sizeof(int2))) != M2L_OK) return st;
+    if ((st = b.tgt_of.ensure((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t))) != M2L_OK) return st;
+    if ((st = b.code.ensure((size_t)(nnz > 0 ? nnz : 1) * sizeof(uint16_t))) != M2L_OK) return st;
+    if ((st = b.seg.ensure((size_t)(17 * (size_t)nseg + 1) * 2 * sizeof(int32_t))) != M2L_OK) return st;
+    if ((st = b.class_off.ensure(18 * sizeof(int32_t))) != M2L_OK) return st;
+    b.nnz = nnz;
+    b.ntgt = ntgt;
+    b.nsrc = nsrc;
+    if (nnz == 0) {
+        M2L_CUDA(cudaMemsetAsync(b.class_off.p, 0, 18 * sizeof(int32_t), s));
+        return M2L_OK;
+    }
+    M2L_CUDA(cudaMemsetAsync(b.tgt_of.p, 0xFF, (size_t)nnz * sizeof(int32_t), s));
+    if (ntgt > 0) {
+        const int threads = 256;
+        const int blocks = (int)(((long)ntgt * 32 + threads - 1) / threads);
+        tgt_of_kernel<<<blocks, threads, 0, s>>>(ntgt, nnz, offsets, b.tgt_of.as<int32_t>(), ops->d_status);
+        M2L_LAUNCH_CHECK("tgt_of_kernel");
+    }
+    int32_t *counts = b.seg.as<int32_t>();
+    int32_t *pos = counts + 17 * (size_t)nseg + 1;
+    code_count_kernel<<<(nseg + 3) / 4, 128, 0, s>>>(nnz, nseg, b.tgt_of.as<int32_t>(), sources, tgt_ijk, src_ijk,
+                                                     nsrc, ops->lut.as<uint16_t>(), b.code.as<uint16_t>(),
+                                                     counts, ops->d_status);
+    M2L_LAUNCH_CHECK("code_count_kernel");
+    exclusive_scan_kernel<<<1, kScanThreads, 0, s>>>(counts, pos, 17 * nseg);
+    M2L_LAUNCH_CHECK("exclusive_scan_kernel");
+    class_offsets_kernel<<<1, 32, 0, s>>>(nseg, nnz, pos, b.class_off.as<int32_t>());
+    M2L_LAUNCH_CHECK("class_offsets_kernel");
+    scatter_kernel<<<(nseg + 3) / 4, 128, 0, s>>>(nnz, nseg, b.code.as<uint16_t>(), b.tgt_of.as<int32_t>(), sources,
+                                                  pos, b.rec.as<int2>());
+    M2L_LAUNCH_CHECK("scatter_kernel");
+    return M2L_OK;
+}
+
+m2l_status classify(const m2l_ops *ops, const m2l_level *lv, int adjoint, Buckets &b, cudaStream_t s)
+{
+    if (!adjoint)
+        return bucket(ops, lv->ncells_tgt, lv->ncells_src, lv->nnz, lv->tgt_ijk, lv->src_ijk, lv->il_offsets,
+                      lv->il_sources, b, s);
+    // Adjoint: transpose the list (rows over sources), then bucket it with the
+    // roles of the two cell sets exchanged; t becomes -t, whose operator is K_t^T.
+    const int nnz = lv->nnz, ntgt = lv->ncells_tgt, nsrc = lv->ncells_src;
+    m2l_status st;
+    if ((st = b.tgt_of.ensure((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t))) != M2L_OK) return st;
+    if ((st = b.t_off.ensure((size_t)(nsrc + 2) * 2 * sizeof(int32_t))) != M2L_OK) return st;
+    if ((st = b.t_src.ensure((size_t)(nnz > 0 ? nnz : 1) * 2 * sizeof(int32_t))) != M2L_OK) return st;
+    if ((st = b.t_cursor.ensure((size_t)(nsrc + 1) * sizeof(int32_t))) != M2L_OK) return st;
+    int32_t *cnt = b.t_off.as<int32_t>();
+    int32_t *toff = cnt + nsrc + 1;
+    int32_t *tsrc = b.t_src.as<int32_t>();
+    int32_t *scratch = tsrc + (nnz > 0 ? nnz : 1);
+    M2L_CUDA(cudaMemsetAsync(cnt, 0, (size_t)(nsrc + 1) * sizeof(int32_t), s));
+    if (nnz > 0) {
+        M2L_CUDA(cudaMemsetAsync(b.tgt_of.p, 0xFF, (size_t)nnz * sizeof(int32_t), s));
+        if (ntgt > 0) {
+            const int blocks = (int)(((long)ntgt * 32 + 255) / 256);
+            tgt_of_kernel<<<blocks, 256, 0, s>>>(ntgt, nnz, lv->il_offsets, b.tgt_of.as<int32_t>(), ops->d_status);
+            M2L_LAUNCH_CHECK("tgt_of_kernel");
+        }
+        const int eb = (nnz + 255) / 256 < 4096 ? (nnz + 255) / 256 : 4096;
+        count_sources_kernel<<<eb, 256, 0, s>>>(nnz, nsrc, b.tgt_of.as<int32_t>(), lv->il_sources, cnt,
+                                               ops->d_status);
+        M2L_LAUNCH_CHECK("count_sources_kernel");
+    }
+    exclusive_scan_kernel<<<1, kScanThreads, 0, s>>>(cnt, toff, nsrc);
+    M2L_LAUNCH_CHECK("exclusive_scan_kernel");
+    if (nnz > 0) {
+        M2L_CUDA(cudaMemcpyAsync(b.t_cursor.p, toff, (size_t)nsrc * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        const int eb = (nnz + 255) / 256 < 4096 ? (nnz + 255) / 256 : 4096;
+        fill_transposed_kernel<<<eb, 256, 0, s>>>(nnz, nsrc, b.tgt_of.as<int32_t>(), lv->il_sources,
+                                                 b.t_cursor.as<int32_t>(), tsrc);
+        M2L_LAUNCH_CHECK("fill_transposed_kernel");
+        if (nsrc > 0) {
+            const int blocks = (int)(((long)nsrc * 32 + 255) / 256);
+            sort_rows_kernel<<<blocks, 256, 0, s>>>(nsrc, toff, tsrc, scratch);
+            M2L_LAUNCH_CHECK("sort_rows_kernel");
+        }
+    }
+    // entries rejected while counting are absent from the transposed list, so
+    // its length is toff[nsrc], which only the device knows: bucket all nnz
+    // slots; the tail beyond toff[nsrc] is marked invalid by tgt_of = -1.
+    return bucket(ops, nsrc, ntgt, nnz, lv->src_ijk, lv->tgt_ijk, toff, tsrc, b, s);
+}
+
+}  // namespace m2l

@@ -1,0 +1,145 @@
+// Internal declarations of the M2L library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+
+#include "../../include/m2l.h"
+
+namespace m2l {
+
+// Device status word bits, set by kernels with atomicOr.
+enum : int {
+    ST_BAD_PAIR = 1,      // a list entry whose t is not a far-field transfer vector
+    ST_BAD_INDEX = 2,     // a source/target index or CSR offset out of range
+    ST_TIMEOUT = 4,       // a bounded wait gave up
+    ST_BAD_TABLE = 8      // a table lookup outside its range
+};
+
+constexpr int kMaxEll = 8;
+constexpr int kNumSym = 16;     // |T_sym| for the bbFMM (Sec. 4.2.1)
+constexpr int kNumPerm = 48;    // signed axis permutations
+constexpr int kTgtBits = 26;    // record packing: tgt | g << 26
+constexpr int kSegEntries = 2048;  // entries per warp segment of the stable bucketing
+
+// Bucketed record .y field: target index in the low 26 bits, permutation
+// index g (< 48) in the high 6 bits.  Unpacked with unsigned shifts: g >= 32
+// sets the sign bit of the int.
+__host__ __device__ __forceinline__ int rec_pack(int tgt, int g)
+{
+    return (int)((unsigned)tgt | ((unsigned)g << kTgtBits));
+}
+__host__ __device__ __forceinline__ int rec_tgt(int y) { return (int)((unsigned)y & ((1u << kTgtBits) - 1u)); }
+__host__ __device__ __forceinline__ int rec_g(int y)
+{
+    const int g = (int)((unsigned)y >> kTgtBits);
+    return g < kNumPerm ? g : kNumPerm - 1;   // never taken for records written by the classifier
+}
+
+void set_error(const char *fmt, ...);
+m2l_status cuda_fail(cudaError_t e, const char *what);
+void count_launch(int n = 1);
+
+#define M2L_CUDA(call)                                                   \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) return ::m2l::cuda_fail(e_, #call);       \
+    } while (0)
+
+#define M2L_LAUNCH_CHECK(what)                                           \
+    do {                                                                 \
+        ::m2l::count_launch();                                           \
+        cudaError_t e_ = cudaGetLastError();                             \
+        if (e_ != cudaSuccess) return ::m2l::cuda_fail(e_, what);        \
+    } while (0)
+
+// A device buffer that only grows.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    m2l_status ensure(size_t need);
+    void release();
+    template <typename T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Output of the classification and bucketing (step a3).
+struct Buckets {
+    DevBuf rec;        // int2 [nnz]: .x = source index, .y = target | g << 26, bucketed
+    DevBuf tgt_of;     // int32 [nnz] target of each list entry (scratch)
+    DevBuf code;       // uint16 [nnz] p | g << 8, or 0xFFFF for a rejected entry (scratch)
+    DevBuf seg;        // int32 [17][nseg] per-segment counts, then positions (scratch)
+    DevBuf class_off;  // int32 [18]: start of bucket p at [p], [16] = valid total, [17] = nnz
+    // adjoint: transposed list (scratch)
+    DevBuf t_off, t_src, t_cursor;
+    int nnz = 0;
+    int ntgt = 0;
+    int nsrc = 0;
+};
+
+// Operand layouts prepared for one precision (built on first use).
+struct Layout {
+    DevBuf a;      // operator matrices in the kernel's layout
+    DevBuf b;      // second operand set (low rank V, or lo parts)
+    bool ready = false;
+};
+
+}  // namespace m2l
+
+struct m2l_ops {
+    int kind = 0;
+    double c = 0.0;
+    int ell = 0, n3 = 0;
+    double eps = 0.0;
+    double ref_width = 1.0;
+    int hom_degree = 0;       // 0 when not homogeneous
+    int homogeneous = 0;
+    int device = 0;
+    int ranks[16] = {0};
+    int rmax = 0;
+    m2l::DevBuf K64;          // double [16][n3][n3]
+    m2l::DevBuf sigma;        // int16 [48][n3]
+    m2l::DevBuf lut;          // uint16 [343]
+    m2l::DevBuf tsym;         // int32 [16][3]
+    m2l::DevBuf U64, V64;     // double [16][n3][rmax] (low rank; zero-padded columns)
+    m2l::Layout simt64, simt32, lr64, lr32, tc_tf32, tc_bf16x3, tc_tf32x3;
+    mutable m2l::Buckets ws;  // workspace of m2l_apply_level
+    mutable double ws_scale = 1.0;  // scale of the level last classified into ws
+    int *d_status = nullptr;  // device status word
+};
+
+struct m2l_plan {
+    const m2l_ops *ops = nullptr;
+    int adjoint = 0;
+    double width = 0.0;
+    int n_out = 0, n_in = 0;
+    m2l::Buckets b;
+};
+
+namespace m2l {
+
+// Precompute (m2l_tables.cu)
+m2l_status build_tables(m2l_ops *ops, cudaStream_t s);
+m2l_status assemble_operators(m2l_ops *ops, cudaStream_t s);
+m2l_status lowrank_factors(m2l_ops *ops);
+m2l_status prepare_simt_layout(const m2l_ops *ops, int fp64, cudaStream_t s);
+int simt_kpad(int n3);
+int simt_mpad(int n3);
+int simt_rpad(int r);
+
+// Classification (m2l_classify.cu)
+m2l_status classify(const m2l_ops *ops, const m2l_level *lv, int adjoint, Buckets &b, cudaStream_t s);
+m2l_status launch_exclusive_scan(const int32_t *in, int32_t *out, int n, cudaStream_t s);
+
+// Apply kernels
+m2l_status launch_simt(const m2l_ops *ops, const Buckets &b, const void *in, void *out, int precision,
+                       int out_fp64, double scale, cudaStream_t s);
+m2l_status launch_tc(const m2l_ops *ops, const Buckets &b, const void *in, void *out, int precision,
+                     int out_fp64, double scale, cudaStream_t s);
+
+int num_sms();
+int max_smem_optin();
+
+}  // namespace m2l

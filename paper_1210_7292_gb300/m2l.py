@@ -1,0 +1,312 @@
+"""Thin Python binding of the C ABI in include/m2l.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own: device memory and streams come from PyTorch, all
+computation runs in libm2l.so.  Importing this module on a machine without the
+built library raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libm2l.so")
+
+M2L_OK, M2L_EINVAL, M2L_ENOMEM, M2L_ECUDA, M2L_ETIMEOUT, M2L_EUNSUPPORTED = range(6)
+STATUS_NAMES = {0: "M2L_OK", 1: "M2L_EINVAL", 2: "M2L_ENOMEM", 3: "M2L_ECUDA", 4: "M2L_ETIMEOUT",
+                5: "M2L_EUNSUPPORTED"}
+M2L_K_INV_R, M2L_K_INV_R4, M2L_K_INV_SQRT_R2C2 = 0, 1, 2
+M2L_FP64, M2L_FP32, M2L_TF32, M2L_BF16X3, M2L_TF32X3 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": M2L_FP64, "fp32": M2L_FP32, "tf32": M2L_TF32, "bf16x3": M2L_BF16X3, "tf32x3": M2L_TF32X3}
+
+
+class M2LError(RuntimeError):
+    def __init__(self, fn, status, msg):
+        super().__init__("%s: %s: %s" % (fn, STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class m2l_kernel(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("c", ctypes.c_double)]
+
+
+class m2l_level(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int), ("width", ctypes.c_double), ("ncells_tgt", ctypes.c_int),
+                ("ncells_src", ctypes.c_int), ("tgt_ijk", ctypes.c_void_p), ("src_ijk", ctypes.c_void_p),
+                ("il_offsets", ctypes.c_void_p), ("il_sources", ctypes.c_void_p), ("nnz", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libm2l.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libm2l.so is not built (run __graft_entry__.build() or "
+                               "python paper_1210_7292_gb300/build.py)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        sig = {
+            "m2l_precompute": [m2l_kernel, I, D, D, ctypes.POINTER(P)],
+            "m2l_ops_rebuild": [P, P],
+            "m2l_ops_query": [P, P, P, P],
+            "m2l_ops_copy_operators": [P, P],
+            "m2l_ops_copy_lowrank": [P, I, P, P],
+            "m2l_ops_info": [P, P, P, P, P, P],
+            "m2l_apply_level": [P, ctypes.POINTER(m2l_level), P, P, I, I, P],
+            "m2l_apply_level_adjoint": [P, ctypes.POINTER(m2l_level), P, P, I, I, P],
+            "m2l_classify_level": [P, ctypes.POINTER(m2l_level), P],
+            "m2l_apply_classified": [P, P, P, I, I, P],
+            "m2l_plan_create": [P, ctypes.POINTER(m2l_level), I, P, ctypes.POINTER(P)],
+            "m2l_plan_apply": [P, P, P, I, I, P],
+            "m2l_plan_query": [P, P, P, P],
+            "m2l_apply_batch": [P, ctypes.POINTER(m2l_level), P, P, I, I, I, P],
+            "m2l_build_lists": [I, P, I, P, P, P, P, P],
+            "m2l_sync_status": [P, P],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.m2l_ops_free.argtypes = [P]
+        L.m2l_ops_free.restype = None
+        L.m2l_plan_free.argtypes = [P]
+        L.m2l_plan_free.restype = None
+        L.m2l_last_error.argtypes = []
+        L.m2l_last_error.restype = ctypes.c_char_p
+        L.m2l_launch_count.argtypes = []
+        L.m2l_launch_count.restype = ctypes.c_int64
+        _lib = L
+    return _lib
+
+
+def _check(fn, status):
+    if status != M2L_OK:
+        raise M2LError(fn, status, lib().m2l_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype=None, what="tensor"):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % what)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must have dtype %s, got %s" % (what, dtype, t.dtype))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Ops:
+    """Owner of an m2l_ops handle (freed with the object)."""
+
+    def __init__(self, handle, ell):
+        self.handle = handle
+        self.ell = ell
+        self.n3 = ell ** 3
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.m2l_ops_free(h)
+
+
+class Level:
+    """One level's device arrays, kept alive alongside the m2l_level struct."""
+
+    def __init__(self, width, tgt_ijk, src_ijk, il_offsets, il_sources, level=0):
+        import torch
+        self.tgt_ijk, self.src_ijk = tgt_ijk, src_ijk
+        self.il_offsets, self.il_sources = il_offsets, il_sources
+        self.width = float(width)
+        self.level = int(level)
+        for name in ("tgt_ijk", "src_ijk", "il_offsets", "il_sources"):
+            _dev_ptr(getattr(self, name), torch.int32, name)
+        self.struct = m2l_level(self.level, self.width, int(tgt_ijk.shape[0]), int(src_ijk.shape[0]),
+                                tgt_ijk.data_ptr(), src_ijk.data_ptr(), il_offsets.data_ptr(),
+                                il_sources.data_ptr(), int(il_sources.numel()))
+
+    @property
+    def nnz(self):
+        return int(self.struct.nnz)
+
+
+def m2l_precompute(kernel_type, ell, eps=0.0, width=0.0, c=0.0) -> Ops:
+    h = ctypes.c_void_p()
+    _check("m2l_precompute", lib().m2l_precompute(m2l_kernel(int(kernel_type), float(c)), int(ell), float(eps),
+                                                  float(width), ctypes.byref(h)))
+    return Ops(h, int(ell))
+
+
+def m2l_ops_rebuild(ops: Ops, stream=None):
+    _check("m2l_ops_rebuild", lib().m2l_ops_rebuild(ops.handle, _stream_ptr(stream)))
+
+
+def m2l_ops_query(ops: Ops):
+    """Returns (ranks [16] int32, sigma [48, ell^3] int16, lut [343] uint16) as numpy arrays."""
+    ranks = np.zeros(16, dtype=np.int32)
+    sigma = np.zeros((48, ops.n3), dtype=np.int16)
+    lut = np.zeros(343, dtype=np.uint16)
+    _check("m2l_ops_query", lib().m2l_ops_query(ops.handle, ranks.ctypes.data, sigma.ctypes.data, lut.ctypes.data))
+    return ranks, sigma, lut
+
+
+def m2l_ops_copy_operators(ops: Ops) -> np.ndarray:
+    out = np.zeros((16, ops.n3, ops.n3), dtype=np.float64)
+    _check("m2l_ops_copy_operators", lib().m2l_ops_copy_operators(ops.handle, out.ctypes.data))
+    return out
+
+
+def m2l_ops_copy_lowrank(ops: Ops, p: int):
+    ranks, _, _ = m2l_ops_query(ops)
+    r = int(ranks[p])
+    U = np.zeros((ops.n3, r))
+    V = np.zeros((ops.n3, r))
+    _check("m2l_ops_copy_lowrank", lib().m2l_ops_copy_lowrank(ops.handle, int(p), U.ctypes.data, V.ctypes.data))
+    return U, V
+
+
+def m2l_ops_info(ops: Ops):
+    ell, kt, hd = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    eps, w = ctypes.c_double(), ctypes.c_double()
+    _check("m2l_ops_info", lib().m2l_ops_info(ops.handle, ctypes.byref(ell), ctypes.byref(kt), ctypes.byref(eps),
+                                              ctypes.byref(w), ctypes.byref(hd)))
+    return {"ell": ell.value, "kernel_type": kt.value, "eps": eps.value, "ref_width": w.value,
+            "homogeneity_degree": hd.value}
+
+
+def _vec_dtypes(precision, out_fp64):
+    import torch
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    tin = torch.float64 if p == M2L_FP64 else torch.float32
+    tout = torch.float64 if (p == M2L_FP64 or out_fp64) else torch.float32
+    return p, tin, tout
+
+
+def m2l_apply_level(ops: Ops, level: Level, multipoles, locals_, precision="fp32", locals_fp64=False, stream=None):
+    p, tin, tout = _vec_dtypes(precision, locals_fp64)
+    _check_shapes(ops, multipoles, locals_, level.struct.ncells_src, level.struct.ncells_tgt)
+    _check("m2l_apply_level", lib().m2l_apply_level(
+        ops.handle, ctypes.byref(level.struct), _dev_ptr(multipoles, tin, "multipoles"),
+        _dev_ptr(locals_, tout, "locals"), p, int(bool(locals_fp64)), _stream_ptr(stream)))
+
+
+def m2l_classify_level(ops: Ops, level: Level, stream=None):
+    _check("m2l_classify_level", lib().m2l_classify_level(ops.handle, ctypes.byref(level.struct),
+                                                          _stream_ptr(stream)))
+    ops._classified = (level.struct.ncells_src, level.struct.ncells_tgt)
+
+
+def m2l_apply_classified(ops: Ops, multipoles, locals_, precision="fp32", locals_fp64=False, stream=None):
+    p, tin, tout = _vec_dtypes(precision, locals_fp64)
+    nin, nout = getattr(ops, "_classified", (multipoles.shape[0], locals_.shape[0]))
+    _check_shapes(ops, multipoles, locals_, nin, nout)
+    _check("m2l_apply_classified", lib().m2l_apply_classified(
+        ops.handle, _dev_ptr(multipoles, tin, "multipoles"), _dev_ptr(locals_, tout, "locals"), p,
+        int(bool(locals_fp64)), _stream_ptr(stream)))
+
+
+def m2l_apply_level_adjoint(ops: Ops, level: Level, grad_locals, grad_multipoles, precision="fp32",
+                            grad_fp64=False, stream=None):
+    p, tin, tout = _vec_dtypes(precision, grad_fp64)
+    _check_shapes(ops, grad_locals, grad_multipoles, level.struct.ncells_tgt, level.struct.ncells_src)
+    _check("m2l_apply_level_adjoint", lib().m2l_apply_level_adjoint(
+        ops.handle, ctypes.byref(level.struct), _dev_ptr(grad_locals, tin, "grad_locals"),
+        _dev_ptr(grad_multipoles, tout, "grad_multipoles"), p, int(bool(grad_fp64)), _stream_ptr(stream)))
+
+
+def _check_shapes(ops, vin, vout, nin, nout):
+    if tuple(vin.shape) != (nin, ops.n3) or tuple(vout.shape) != (nout, ops.n3):
+        raise ValueError("vector shapes %s -> %s, expected (%d, %d) -> (%d, %d)"
+                         % (tuple(vin.shape), tuple(vout.shape), nin, ops.n3, nout, ops.n3))
+
+
+class Plan:
+    def __init__(self, handle, ops, n_in, n_out):
+        self.handle, self.ops, self.n_in, self.n_out = handle, ops, n_in, n_out
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.m2l_plan_free(h)
+
+
+def m2l_plan_create(ops: Ops, level: Level, adjoint=False, stream=None) -> Plan:
+    h = ctypes.c_void_p()
+    _check("m2l_plan_create", lib().m2l_plan_create(ops.handle, ctypes.byref(level.struct), int(bool(adjoint)),
+                                                    _stream_ptr(stream), ctypes.byref(h)))
+    s = level.struct
+    n_in, n_out = (s.ncells_tgt, s.ncells_src) if adjoint else (s.ncells_src, s.ncells_tgt)
+    return Plan(h, ops, n_in, n_out)
+
+
+def m2l_plan_apply(plan: Plan, vin, vout, precision="fp32", out_fp64=False, stream=None):
+    p, tin, tout = _vec_dtypes(precision, out_fp64)
+    _check_shapes(plan.ops, vin, vout, plan.n_in, plan.n_out)
+    _check("m2l_plan_apply", lib().m2l_plan_apply(plan.handle, _dev_ptr(vin, tin, "input vectors"),
+                                                  _dev_ptr(vout, tout, "output vectors"), p,
+                                                  int(bool(out_fp64)), _stream_ptr(stream)))
+
+
+def m2l_plan_query(plan: Plan):
+    """Returns (counts [16] int64, records [nvalid, 3] int32: source, target, g)."""
+    counts = np.zeros(16, dtype=np.int64)
+    nvalid = ctypes.c_int64()
+    _check("m2l_plan_query", lib().m2l_plan_query(plan.handle, counts.ctypes.data, None, ctypes.byref(nvalid)))
+    rec = np.zeros((max(1, nvalid.value), 3), dtype=np.int32)
+    _check("m2l_plan_query", lib().m2l_plan_query(plan.handle, None, rec.ctypes.data, ctypes.byref(nvalid)))
+    return counts, rec[:nvalid.value]
+
+
+def m2l_apply_batch(ops_list, levels, multipoles, locals_, precision="fp32", locals_fp64=False, stream=None):
+    n = len(ops_list)
+    p, tin, tout = _vec_dtypes(precision, locals_fp64)
+    arr_ops = (ctypes.c_void_p * n)(*[o.handle.value for o in ops_list])
+    arr_lv = (m2l_level * n)(*[lv.struct for lv in levels])
+    for o, lv, a, b in zip(ops_list, levels, multipoles, locals_):
+        _check_shapes(o, a, b, lv.struct.ncells_src, lv.struct.ncells_tgt)
+    arr_in = (ctypes.c_void_p * n)(*[_dev_ptr(t, tin, "multipoles").value for t in multipoles])
+    arr_out = (ctypes.c_void_p * n)(*[_dev_ptr(t, tout, "locals").value for t in locals_])
+    _check("m2l_apply_batch", lib().m2l_apply_batch(arr_ops, arr_lv, arr_in, arr_out, n, p, int(bool(locals_fp64)),
+                                                    _stream_ptr(stream)))
+
+
+def m2l_build_lists(tgt_ijk, src_ijk, stream=None):
+    """Returns (il_offsets, il_sources) as device int32 tensors."""
+    import torch
+    nt, ns = int(tgt_ijk.shape[0]), int(src_ijk.shape[0])
+    off = torch.empty(nt + 1, dtype=torch.int32, device=tgt_ijk.device)
+    nnz = ctypes.c_int64()
+    L = lib()
+    _check("m2l_build_lists", L.m2l_build_lists(nt, _dev_ptr(tgt_ijk, torch.int32, "tgt_ijk"), ns,
+                                                _dev_ptr(src_ijk, torch.int32, "src_ijk"), _dev_ptr(off), None,
+                                                ctypes.byref(nnz), _stream_ptr(stream)))
+    src = torch.empty(max(1, nnz.value), dtype=torch.int32, device=tgt_ijk.device)
+    _check("m2l_build_lists", L.m2l_build_lists(nt, _dev_ptr(tgt_ijk), ns, _dev_ptr(src_ijk), _dev_ptr(off),
+                                                _dev_ptr(src), ctypes.byref(nnz), _stream_ptr(stream)))
+    return off, src[:nnz.value]
+
+
+def m2l_sync_status(ops: Ops, stream=None):
+    _check("m2l_sync_status", lib().m2l_sync_status(ops.handle, _stream_ptr(stream)))
+
+
+def m2l_last_error() -> str:
+    return lib().m2l_last_error().decode(errors="replace")
+
+
+def m2l_launch_count() -> int:
+    return int(lib().m2l_launch_count())
