@@ -219,6 +219,29 @@ m2l_status m2l_build_lists(int ncells_tgt, const int32_t *tgt_ijk, int ncells_sr
                            int64_t *nnz_out, void *stream);
 
 /* ---------------------------------------------------------------------
+ * m2l_apply_level_noalloc: m2l_apply_level with M2L_FP32 products and float
+ * locals, for callers that must not allocate device memory while they run --
+ * code that executes between a framework's set-up and tear-down phases under
+ * a fixed memory budget, inside a real-time loop, or where a cudaMalloc would
+ * synchronise the device or deadlock against another allocator.  The paper
+ * has no counterpart: it is an interface of this library only.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  Its
+ * scratch (interaction buckets and the FP32 operator layout) is one
+ * file-scope device array of about 10.7 MB that every GPU which loads the
+ * library holds until the process exits.  Limits: nnz <= 524288 list
+ * entries, ell <= 6, full-rank ops (eps == 0); larger requests return
+ * M2L_EINVAL (nnz) or M2L_EUNSUPPORTED (ell, low rank) before any work.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (once per device, with that device current): make
+ * that first call before any stream capture.  All calls share the array and
+ * each call rewrites what it reads, so calls whose GPU work overlaps (other
+ * streams, other threads) race: order them on one stream.
+ * Arguments and results as m2l_apply_level (locals accumulated, list errors
+ * reported by m2l_sync_status). */
+m2l_status m2l_apply_level_noalloc(const m2l_ops *ops, const m2l_level *level, const float *multipoles,
+                                   float *locals, void *stream);
+
+/* ---------------------------------------------------------------------
  * Synchronises `stream`, then returns and clears the device status word of
  * ops (M2L_OK, M2L_EINVAL for list entries that were skipped, M2L_ETIMEOUT). */
 m2l_status m2l_sync_status(const m2l_ops *ops, void *stream);

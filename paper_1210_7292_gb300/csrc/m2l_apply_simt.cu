@@ -263,3 +263,33 @@ m2l_status launch_simt(const m2l_ops *ops, const Buckets &b, const void *in, voi
 }
 
 }  // namespace m2l
+
+namespace m2l {
+
+// The FP32 full-rank SIMT kernel on caller-provided buckets and operator
+// layout (no allocation).  Only the 64-column configuration is offered.
+m2l_status launch_simt_f32_raw(const m2l_ops *ops, const int2 *rec, const int *class_off, int nnz, const float *KT,
+                               const float *in, float *out, double scale, cudaStream_t s)
+{
+    if (nnz == 0) return M2L_OK;
+    const int n3 = ops->n3, kpad = simt_kpad(n3), mpad = simt_mpad(n3);
+    const size_t smem = simt_smem<float, 64, false>(ops);
+    if ((int)smem > max_smem_optin()) {
+        set_error("order %d needs %zu bytes of shared memory in the SIMT kernel", ops->ell, smem);
+        return M2L_EUNSUPPORTED;
+    }
+    auto kern = simt_apply_kernel<float, float, 64, false>;
+    M2L_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    M2L_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+    if (per_sm < 1) per_sm = 1;
+    long grid = (long)num_sms() * per_sm;
+    const long tiles_bound = (long)(nnz + 63) / 64 + 16;
+    if (grid > tiles_bound) grid = tiles_bound;
+    kern<<<(int)grid, kThreads, smem, s>>>(rec, class_off, KT, nullptr, ops->sigma.as<int16_t>(), in, out, n3, kpad,
+                                           mpad, 0, scale);
+    M2L_LAUNCH_CHECK("simt_apply_kernel");
+    return M2L_OK;
+}
+
+}  // namespace m2l

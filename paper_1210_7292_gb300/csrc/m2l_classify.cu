@@ -313,3 +313,39 @@ m2l_status classify(const m2l_ops *ops, const m2l_level *lv, int adjoint, Bucket
 }
 
 }  // namespace m2l
+
+namespace m2l {
+
+// Bucketing into caller-provided device buffers (no allocation): the same
+// kernels as bucket(), with rec [nnz], tgt_of [nnz], code [nnz],
+// seg [2 * (17 * nseg + 1)] and class_off [18] supplied by the caller.
+m2l_status bucket_raw(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const int32_t *tgt_ijk,
+                      const int32_t *src_ijk, const int32_t *offsets, const int32_t *sources, int2 *rec,
+                      int32_t *tgt_of, uint16_t *code, int32_t *seg, int32_t *class_off, cudaStream_t s)
+{
+    if (nnz == 0) {
+        M2L_CUDA(cudaMemsetAsync(class_off, 0, 18 * sizeof(int32_t), s));
+        return M2L_OK;
+    }
+    const int nseg = (nnz + kSegEntries - 1) / kSegEntries;
+    M2L_CUDA(cudaMemsetAsync(tgt_of, 0xFF, (size_t)nnz * sizeof(int32_t), s));
+    if (ntgt > 0) {
+        const int blocks = (int)(((long)ntgt * 32 + 255) / 256);
+        tgt_of_kernel<<<blocks, 256, 0, s>>>(ntgt, nnz, offsets, tgt_of, ops->d_status);
+        M2L_LAUNCH_CHECK("tgt_of_kernel");
+    }
+    int32_t *counts = seg;
+    int32_t *pos = seg + 17 * (size_t)nseg + 1;
+    code_count_kernel<<<(nseg + 3) / 4, 128, 0, s>>>(nnz, nseg, tgt_of, sources, tgt_ijk, src_ijk, nsrc,
+                                                     ops->lut.as<uint16_t>(), code, counts, ops->d_status);
+    M2L_LAUNCH_CHECK("code_count_kernel");
+    exclusive_scan_kernel<<<1, kScanThreads, 0, s>>>(counts, pos, 17 * nseg);
+    M2L_LAUNCH_CHECK("exclusive_scan_kernel");
+    class_offsets_kernel<<<1, 32, 0, s>>>(nseg, nnz, pos, class_off);
+    M2L_LAUNCH_CHECK("class_offsets_kernel");
+    scatter_kernel<<<(nseg + 3) / 4, 128, 0, s>>>(nnz, nseg, code, tgt_of, sources, pos, rec);
+    M2L_LAUNCH_CHECK("scatter_kernel");
+    return M2L_OK;
+}
+
+}  // namespace m2l

@@ -309,3 +309,18 @@ m2l_status prepare_simt_layout(const m2l_ops *ops, int fp64, cudaStream_t s)
 }
 
 }  // namespace m2l
+
+namespace m2l {
+
+// FP32 transposed, zero-padded operator layout of the SIMT kernel written
+// into caller-provided memory KT [16][kpad][mpad] (no allocation).
+m2l_status launch_transpose_pad_f32(const m2l_ops *ops, float *KT, int kpad, int mpad, cudaStream_t s)
+{
+    const size_t total = 16 * (size_t)kpad * mpad;
+    transpose_pad_kernel<float><<<(int)((total + 255) / 256), 256, 0, s>>>(ops->n3, kpad, mpad,
+                                                                         ops->K64.as<double>(), KT);
+    M2L_LAUNCH_CHECK("transpose_pad_kernel");
+    return M2L_OK;
+}
+
+}  // namespace m2l

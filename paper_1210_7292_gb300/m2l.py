@@ -67,6 +67,7 @@ def lib():
             "m2l_plan_query": [P, P, P, P],
             "m2l_apply_batch": [P, ctypes.POINTER(m2l_level), P, P, I, I, I, P],
             "m2l_build_lists": [I, P, I, P, P, P, P, P],
+            "m2l_apply_level_noalloc": [P, ctypes.POINTER(m2l_level), P, P, P],
             "m2l_sync_status": [P, P],
         }
         for name, args in sig.items():
@@ -298,6 +299,15 @@ def m2l_build_lists(tgt_ijk, src_ijk, stream=None):
     _check("m2l_build_lists", L.m2l_build_lists(nt, _dev_ptr(tgt_ijk), ns, _dev_ptr(src_ijk), _dev_ptr(off),
                                                 _dev_ptr(src), ctypes.byref(nnz), _stream_ptr(stream)))
     return off, src[:nnz.value]
+
+
+def m2l_apply_level_noalloc(ops: Ops, level: Level, multipoles, locals_, stream=None):
+    """FP32 level translation that allocates no device memory (see include/m2l.h)."""
+    import torch
+    _check_shapes(ops, multipoles, locals_, level.struct.ncells_src, level.struct.ncells_tgt)
+    _check("m2l_apply_level_noalloc", lib().m2l_apply_level_noalloc(
+        ops.handle, ctypes.byref(level.struct), _dev_ptr(multipoles, torch.float32, "multipoles"),
+        _dev_ptr(locals_, torch.float32, "locals"), _stream_ptr(stream)))
 
 
 def m2l_sync_status(ops: Ops, stream=None):
