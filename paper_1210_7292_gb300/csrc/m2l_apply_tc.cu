@@ -3,16 +3,16 @@
 // One persistent CTA per SM walks a contiguous range of tiles; a tile is NT
 // bucketed interactions of one unique operator K_p (Alg. 2, blocked along many
 // target cells as in Sec. 4.2.3).  Warp roles:
-//   warps 0-3  producers: per tile, gather the NT source multipoles and
+//   warps 0-7  producers: per tile, gather the NT source multipoles and
 //              permute them (W_p[sigma_g(b)][c] = w[b], Eq. (30)) straight into
 //              a 128-byte-swizzled K-major shared-memory panel (the UMMA B
 //              operand), rounded to TF32 or split into BF16/TF32 hi + lo;
 //              when the operator changes, one thread copies its pre-swizzled
 //              image (the UMMA A operand) with cp.async.bulk.
-//   warp 4     allocates TMEM and issues tcgen05.mma (one thread):
+//   warp 8     allocates TMEM and issues tcgen05.mma (one thread):
 //              F_p = K_p W_p (Eq. (31)) into a double-buffered TMEM accumulator,
 //              three products hi*hi + hi*lo + lo*hi for the split precisions.
-//   warps 5-8  epilogue: tcgen05.ld of the accumulator, un-permutation
+//   warps 9-16 epilogue (two groups of four, each owning half the columns): tcgen05.ld of the accumulator, un-permutation
 //              f[a] += F_p[sigma_g(a)] (Eq. (32)) through a shared-memory
 //              transpose, sum over the consecutive columns of one target,
 //              one atomic add per (target, node) and run (Alg. 2, third loop).
@@ -26,11 +26,13 @@
 namespace m2l {
 namespace {
 
-constexpr int kProducerWarps = 4;
-constexpr int kMmaWarp = 4;
-constexpr int kEpiWarp0 = 5;
-constexpr int kThreadsTC = 9 * 32;
+constexpr int kProducerWarps = 8;
+constexpr int kMmaWarp = 8;
+constexpr int kEpiWarp0 = 9;
+constexpr int kEpiWarps = 8;
+constexpr int kThreadsTC = (kProducerWarps + 1 + kEpiWarps) * 32;
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+constexpr uint32_t kSuspendHintNs = 20000;         // longest park of one try_wait
 
 enum TcKind : int { TC_TF32 = 0, TC_BF16X3 = 1, TC_TF32X3 = 2 };
 
@@ -67,15 +69,18 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
+// try_wait with a suspend-time hint: a thread whose phase is not complete is
+// parked by the hardware (up to the hint, in ns) instead of spinning, so that
+// waiting warps leave the issue slots to the warps doing the work.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendHintNs)
         : "memory");
     return ok != 0;
 }
@@ -184,21 +189,34 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[N]);
+
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float (&v)[16])
 {
-    uint32_t r[32];
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, float (&v)[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ float tf32_rna(float x)
@@ -230,38 +248,61 @@ __device__ __forceinline__ void tile_info(int t, const int *tile_start, const in
     nc = min(NT, class_off[p + 1] - col0);
 }
 
-template <int KIND>
+template <int KIND, int KATOMS>
 __global__ void __launch_bounds__(kThreadsTC, 1)
 tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
-                const uint8_t *__restrict__ a_img, int a_bytes, const int16_t *__restrict__ sigma,
-                const int16_t *__restrict__ sigma_inv, const float *__restrict__ mp, float *__restrict__ out_f32,
-                double *__restrict__ out_f64, int n3, int katoms, float scale, int *status)
+                const uint8_t *__restrict__ a_img, int a_bytes, const int16_t *__restrict__ sigma_inv,
+                const float *__restrict__ mp, float *__restrict__ out_f32, double *__restrict__ out_f64, int n3,
+                float scale, int *status)
 {
     using Tr = TcTraits<KIND>;
     constexpr int NT = Tr::NT;
-    constexpr int ELEMS_PER_ATOM = 128 / Tr::esz;          // K elements per 128-byte row
-    constexpr int K_PER_MMA = 32 / Tr::esz;                 // 8 (tf32) or 16 (bf16)
+    constexpr int ELEMS_PER_ATOM = 128 / Tr::esz;           // K elements per 128-byte row
+    constexpr int K_PER_MMA = 32 / Tr::esz;                  // 8 (tf32) or 16 (bf16)
     constexpr int MMAS_PER_ATOM = ELEMS_PER_ATOM / K_PER_MMA;  // 4
-    const int a_part_bytes = katoms * 128 * 128;            // one operand part of A (128 rows)
-    const int b_part_bytes = katoms * NT * 128;             // one operand part of a B stage
-    const int b_stage_bytes = b_part_bytes * Tr::nparts;
+    constexpr int EPC = 16 / Tr::esz;                        // elements per 16-byte chunk
+    constexpr int KPAD = KATOMS * ELEMS_PER_ATOM;            // padded K (source nodes)
+    constexpr int CPC = KATOMS * 8;                          // 16-byte chunks per column and part
+    constexpr int NPT = kProducerWarps * 32;                 // producer threads
+    constexpr int NCG = NPT / CPC;                           // column stride of a producer thread
+    constexpr int CPT = (NT + NCG - 1) / NCG;                // columns per producer thread
+    constexpr int A_PART = KATOMS * 128 * 128;               // one operand part of A (128 rows)
+    constexpr int B_PART = KATOMS * NT * 128;                // one operand part of a B stage
+    constexpr int B_STAGE = B_PART * Tr::nparts;
+    constexpr int ECOLS = NT / 2;                            // columns per epilogue group and tile
+    constexpr int ECH = ECOLS < 16 ? ECOLS : 16;             // columns per TMEM load
+    static_assert(NPT % CPC == 0, "producer mapping");
+    static_assert(ECOLS % ECH == 0 && (ECH == 16 || ECH == 8), "epilogue chunking");
 
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t *sA = smem;                                      // a_bytes
-    uint8_t *sB = sA + a_bytes;                              // 2 stages
-    float *sF = reinterpret_cast<float *>(sB + 2 * b_stage_bytes);   // [32][129] epilogue transpose
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sF + 32 * 129);
-    uint64_t *full = bars, *empty = bars + 2, *tfull = bars + 4, *tempty = bars + 6, *afull = bars + 8,
-             *drain = bars + 9;
+    // 1024-byte alignment by offsetting the __shared__ array itself, so that every
+    // access below stays a shared-memory access (an integer round trip would
+    // turn them into generic ones)
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    uint8_t *sA = smem;                                               // a_bytes
+    uint8_t *sB = sA + a_bytes;                                       // 2 stages
+    float *sF = reinterpret_cast<float *>(sB + 2 * B_STAGE);          // [2 groups][ECH][129] transposes
+    int16_t *s_sinv = reinterpret_cast<int16_t *>(sF + 2 * ECH * 129);  // [48][KPAD] inverse permutations
+    int2 *s_prec = reinterpret_cast<int2 *>(s_sinv + 48 * KPAD);      // [2][NT] producer records
+    int2 *s_erec = s_prec + 2 * NT;                                   // [2 groups][2][ECOLS] ints: column tables
+    uint64_t *bars = reinterpret_cast<uint64_t *>(s_erec + NT);
+    uint64_t *full = bars, *empty = bars + 2, *tfull = bars + 4, *tempty = bars + 8, *afull = bars + 12,
+             *drain = bars + 13;
     __shared__ uint32_t s_tmem_base;
     __shared__ int s_abort;
     __shared__ int s_tile_start[17];
     __shared__ TileSched s_sched;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int TMEM_COLS = 2 * NT;
+    constexpr int NACC = 4;                      // TMEM accumulator buffers
+    constexpr int TMEM_COLS = NACC * NT;
 
+    // inverse permutation tables sigma_g^{-1}, rows padded to KPAD with index 0
+    // (padded K rows of the panel meet zero operator columns)
+    for (int idx = threadIdx.x; idx < 48 * KPAD; idx += blockDim.x) {
+        const int g = idx / KPAD, kk = idx % KPAD;
+        s_sinv[idx] = (kk < n3) ? sigma_inv[g * n3 + kk] : (int16_t)0;
+    }
     if (threadIdx.x == 0) {
         int acc = 0;
         for (int p = 0; p < 16; ++p) {
@@ -274,10 +315,12 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
         s_sched.last = min(acc, s_sched.first + per);
         s_abort = 0;
         for (int i = 0; i < 2; ++i) {
-            mbar_init(full + i, kProducerWarps * 32);
+            mbar_init(full + i, NPT);
             mbar_init(empty + i, 1);
+        }
+        for (int i = 0; i < NACC; ++i) {
             mbar_init(tfull + i, 1);
-            mbar_init(tempty + i, 4 * 32);
+            mbar_init(tempty + i, kEpiWarps * 32);
         }
         mbar_init(afull, 1);
         mbar_init(drain, 1);
@@ -298,9 +341,18 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
 
     if (warp < kProducerWarps) {
         // ------------------------------------------------------------ producers
-        const int ptid = threadIdx.x;   // 0..127
+        const int ptid = threadIdx.x;
+        const int j = ptid % CPC;            // 16-byte chunk of the column this thread fills
+        const int cg = ptid / CPC;           // first column of this thread
         int prev_p = -1;
         uint32_t a_loads = 0;
+        // records are fetched one tile ahead, into a register of thread c < NT
+        int2 nxt = make_int2(0, 0);
+        if (first < last && ptid < NT) {
+            int p0, c00, nc0;
+            tile_info(first, s_tile_start, class_off, NT, p0, c00, nc0);
+            if (ptid < nc0) nxt = __ldg(rec + c00 + ptid);
+        }
         for (int t = first; t < last; ++t) {
             const int i = t - first, s = i & 1, k = i >> 1;
             int p, col0, nc;
@@ -317,68 +369,77 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
                 }
                 prev_p = p;
             }
-            if (!mbar_wait(empty + s, (k & 1) ^ 1, abort_flag, status)) break;
-            uint8_t *stage = sB + s * b_stage_bytes;
-            if constexpr (KIND == TC_BF16X3) {
-                // 8 bf16 per 16-byte chunk; half a warp per column
-                const int nchunks = katoms * 8;
-                for (int c = (ptid >> 4); c < NT; c += 8) {
-                    const int2 r = (c < nc) ? rec[col0 + c] : make_int2(0, 0);
-                    const int g = rec_g(r.y);
-                    const float *w = mp + (size_t)r.x * n3;
-                    const int16_t *si = sigma_inv + g * n3;
-                    for (int j = (ptid & 15); j < nchunks; j += 16) {
-                        uint32_t hi[4], lo[4];
+            // records of this tile; the previous tile with this stage is fully consumed
+            int2 *prec = s_prec + s * NT;
+            if (ptid < NT) {
+                prec[ptid] = nxt;
+                nxt = make_int2(0, 0);
+                if (t + 1 < last) {
+                    int p1, c01, nc1;
+                    tile_info(t + 1, s_tile_start, class_off, NT, p1, c01, nc1);
+                    if (ptid < nc1) nxt = __ldg(rec + c01 + ptid);
+                }
+            }
+            named_bar_sync(2, NPT);
+            // issue every gather of this thread before waiting for the stage
+            float v[CPT][EPC];
 #pragma unroll
-                        for (int e = 0; e < 8; e += 2) {
-                            float v[2];
+            for (int u = 0; u < CPT; ++u) {
+                const int c = cg + u * NCG;
+                const bool live = (c < nc);
+                const int2 r = live ? prec[c] : make_int2(0, 0);
+                const float *w = mp + (size_t)r.x * n3;
+                const int16_t *si = s_sinv + rec_g(r.y) * KPAD + EPC * j;
+                int16_t idx[EPC];
+                if constexpr (EPC == 4) {
+                    const uint2 q = *reinterpret_cast<const uint2 *>(si);
+                    idx[0] = (int16_t)(q.x & 0xFFFF); idx[1] = (int16_t)(q.x >> 16);
+                    idx[2] = (int16_t)(q.y & 0xFFFF); idx[3] = (int16_t)(q.y >> 16);
+                } else {
+                    const uint4 q = *reinterpret_cast<const uint4 *>(si);
+                    const uint32_t qq[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-                            for (int q = 0; q < 2; ++q) {
-                                const int kk = 8 * j + e + q;
-                                v[q] = (c < nc && kk < n3) ? __ldg(w + si[kk]) : 0.0f;
-                            }
-                            const __nv_bfloat16 h0 = __float2bfloat16_rn(v[0]);
-                            const __nv_bfloat16 h1 = __float2bfloat16_rn(v[1]);
-                            const __nv_bfloat16 l0 = __float2bfloat16_rn(v[0] - __bfloat162float(h0));
-                            const __nv_bfloat16 l1 = __float2bfloat16_rn(v[1] - __bfloat162float(h1));
-                            hi[e / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                            lo[e / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-                        }
-                        const uint32_t off = (uint32_t)(j >> 3) * (uint32_t)(NT * 128) + swz_off(c, j & 7);
-                        *reinterpret_cast<uint4 *>(stage + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                        *reinterpret_cast<uint4 *>(stage + b_part_bytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                    for (int e = 0; e < 4; ++e) {
+                        idx[2 * e] = (int16_t)(qq[e] & 0xFFFF);
+                        idx[2 * e + 1] = (int16_t)(qq[e] >> 16);
                     }
                 }
-            } else {
-                // 4 fp32 per 16-byte chunk; one warp per column
-                const int nchunks = katoms * 8;
-                for (int c = warp; c < NT; c += kProducerWarps) {
-                    const int2 r = (c < nc) ? rec[col0 + c] : make_int2(0, 0);
-                    const int g = rec_g(r.y);
-                    const float *w = mp + (size_t)r.x * n3;
-                    const int16_t *si = sigma_inv + g * n3;
-                    for (int j = lane; j < nchunks; j += 32) {
-                        float v[4];
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int kk = 4 * j + e;
-                            v[e] = (c < nc && kk < n3) ? __ldg(w + si[kk]) : 0.0f;
-                        }
-                        const uint32_t off = (uint32_t)(j >> 3) * (uint32_t)(NT * 128) + swz_off(c, j & 7);
-                        if constexpr (KIND == TC_TF32) {
-                            *reinterpret_cast<float4 *>(stage + off) =
-                                make_float4(tf32_rna(v[0]), tf32_rna(v[1]), tf32_rna(v[2]), tf32_rna(v[3]));
-                        } else {
-                            float h[4], l[4];
+                for (int e = 0; e < EPC; ++e) v[u][e] = live ? __ldg(w + idx[e]) : 0.0f;
+            }
+            const bool ok = mbar_wait(empty + s, (k & 1) ^ 1, abort_flag, status);
+            if (named_bar_or(2, NPT, ok ? 0 : 1)) break;
+            uint8_t *stage = sB + s * B_STAGE;
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                h[e] = tf32_rna(v[e]);
-                                l[e] = tf32_rna(v[e] - h[e]);
-                            }
-                            *reinterpret_cast<float4 *>(stage + off) = make_float4(h[0], h[1], h[2], h[3]);
-                            *reinterpret_cast<float4 *>(stage + b_part_bytes + off) = make_float4(l[0], l[1], l[2], l[3]);
-                        }
+            for (int u = 0; u < CPT; ++u) {
+                const int c = cg + u * NCG;
+                if (c >= NT) break;
+                const uint32_t off = (uint32_t)(j >> 3) * (uint32_t)(NT * 128) + swz_off(c, j & 7);
+                if constexpr (KIND == TC_BF16X3) {
+                    uint32_t hi[4], lo[4];
+#pragma unroll
+                    for (int e = 0; e < 8; e += 2) {
+                        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[u][e]);
+                        const __nv_bfloat16 h1 = __float2bfloat16_rn(v[u][e + 1]);
+                        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[u][e] - __bfloat162float(h0));
+                        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[u][e + 1] - __bfloat162float(h1));
+                        hi[e / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                        lo[e / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
                     }
+                    *reinterpret_cast<uint4 *>(stage + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                    *reinterpret_cast<uint4 *>(stage + B_PART + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                } else if constexpr (KIND == TC_TF32) {
+                    *reinterpret_cast<float4 *>(stage + off) =
+                        make_float4(tf32_rna(v[u][0]), tf32_rna(v[u][1]), tf32_rna(v[u][2]), tf32_rna(v[u][3]));
+                } else {
+                    float h[4], l[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        h[e] = tf32_rna(v[u][e]);
+                        l[e] = tf32_rna(v[u][e] - h[e]);
+                    }
+                    *reinterpret_cast<float4 *>(stage + off) = make_float4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<float4 *>(stage + B_PART + off) = make_float4(l[0], l[1], l[2], l[3]);
                 }
             }
             fence_proxy_async();
@@ -404,12 +465,15 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
                     ++a_loads;
                     prev_p = p;
                 }
-                if (!mbar_wait(tempty + s, (k & 1) ^ 1, abort_flag, status)) break;
+                const int ab = i & (NACC - 1), ak = i / NACC;
+                if (!mbar_wait(tempty + ab, (ak & 1) ^ 1, abort_flag, status)) break;
                 tc_fence_after();
-                const uint32_t d = tmem_base + (uint32_t)(s * NT);
-                const uint32_t bst = b_base + (uint32_t)(s * b_stage_bytes);
+                const uint32_t d = tmem_base + (uint32_t)(ab * NT);
+                const uint32_t bst = b_base + (uint32_t)(s * B_STAGE);
                 uint32_t accum = 0;
-                for (int ka = 0; ka < katoms; ++ka) {
+#pragma unroll
+                for (int ka = 0; ka < KATOMS; ++ka) {
+#pragma unroll
                     for (int m = 0; m < MMAS_PER_ATOM; ++m) {
                         const uint32_t koff = (uint32_t)(m * 32);
                         const uint32_t a0 = a_base + (uint32_t)(ka * 128 * 128) + koff;
@@ -418,13 +482,13 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
                         accum = 1;
                         if constexpr (Tr::nprod == 3) {
                             // hi*lo and lo*hi into the same accumulator
-                            umma<KIND>(d, smem_desc(a0), smem_desc(b0 + (uint32_t)b_part_bytes), idesc, 1);
-                            umma<KIND>(d, smem_desc(a0 + (uint32_t)a_part_bytes), smem_desc(b0), idesc, 1);
+                            umma<KIND>(d, smem_desc(a0), smem_desc(b0 + (uint32_t)B_PART), idesc, 1);
+                            umma<KIND>(d, smem_desc(a0 + (uint32_t)A_PART), smem_desc(b0), idesc, 1);
                         }
                     }
                 }
                 umma_commit(empty + s);
-                umma_commit(tfull + s);
+                umma_commit(tfull + ab);
                 issued = true;
             }
             if (issued) {
@@ -436,48 +500,90 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue
-        const int q = warp & 3;               // TMEM lane quarter this warp may read
-        const int row = 32 * q + lane;        // accumulator row (permuted node a')
-        const int a = threadIdx.x - kEpiWarp0 * 32;   // output node handled in the reduction
-        const int16_t *sg_base = sigma;
+        // two groups of four warps; group G owns columns [G*ECOLS, (G+1)*ECOLS) of every tile
+        const int et = threadIdx.x - kEpiWarp0 * 32;   // 0..255
+        const int G = et >> 7;
+        const int a = et & 127;                        // output node handled in the reduction
+        const int q = warp & 3;                        // TMEM lane quarter this warp may read
+        const int row = 32 * q + lane;                 // accumulator row (permuted node a')
+        const int bar_id = 1 + 2 * G;                  // named barriers 1 and 3
+        float *sFg = sF + G * ECH * 129;
+        int *e_goff = reinterpret_cast<int *>(s_erec) + G * 2 * ECOLS;   // [ECOLS] g * KPAD per column
+        int *e_tgt = e_goff + ECOLS;                                      // [ECOLS] target, -1 when dead
         int cur = -1;
         float acc = 0.0f;
+        const int gc0 = G * ECOLS;                        // first tile column of this group
+        // records are fetched one tile ahead, into a register of thread a < ECOLS (y = -1: dead column)
+        int nxt = -1;
+        if (first < last && a < ECOLS) {
+            int p0, c00, nc0;
+            tile_info(first, s_tile_start, class_off, NT, p0, c00, nc0);
+            if (a < nc0 - gc0) nxt = __ldg(rec + c00 + gc0 + a).y;
+        }
         for (int t = first; t < last; ++t) {
-            const int i = t - first, s = i & 1, k = i >> 1;
+            const int i = t - first, ab = i & (NACC - 1), ak = i / NACC;
             int p, col0, nc;
             tile_info(t, s_tile_start, class_off, NT, p, col0, nc);
-            // all four epilogue warps leave together if any of them gave up
-            const bool ok = mbar_wait(tfull + s, k & 1, abort_flag, status);
-            if (named_bar_or(1, 128, ok ? 0 : 1)) break;
-            tc_fence_after();
-            for (int ch = 0; ch < NT / 32; ++ch) {
-                float v[32];
-                tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(s * NT + 32 * ch), v);
-                if (ch == NT / 32 - 1) {
-                    tc_fence_before();
-                    mbar_arrive(tempty + s);
+            const int gnc = min(ECOLS, nc - gc0);         // live columns of this group (may be <= 0)
+            if (a < ECOLS) {
+                e_goff[a] = (nxt == -1 ? 0 : rec_g(nxt)) * KPAD;
+                e_tgt[a] = (nxt == -1) ? -1 : rec_tgt(nxt);
+                nxt = -1;
+                if (t + 1 < last) {
+                    int p1, c01, nc1;
+                    tile_info(t + 1, s_tile_start, class_off, NT, p1, c01, nc1);
+                    if (a < nc1 - gc0) nxt = __ldg(rec + c01 + gc0 + a).y;
                 }
+            }
+            // all four warps of the group leave together if any of them gave up
+            const bool ok = mbar_wait(tfull + ab, ak & 1, abort_flag, status);
+            if (named_bar_or(bar_id, 128, ok ? 0 : 1)) break;
+            tc_fence_after();
+#pragma unroll 1
+            for (int ch = 0; ch < ECOLS / ECH; ++ch) {
+                float v[ECH];
+                tmem_ld<ECH>(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * NT + gc0 + ECH * ch), v);
+                if (ch == ECOLS / ECH - 1) {
+                    tc_fence_before();
+                    mbar_arrive(tempty + ab);
+                }
+                // un-permute on the write: row a' of column jj lands at node sigma_g^{-1}(a')
+                if (row < n3) {
+                    int go[ECH];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) sF[j * 129 + row] = v[j];
-                named_bar_sync(1, 128);
+                    for (int v4 = 0; v4 < ECH / 4; ++v4) {
+                        const int4 x = *reinterpret_cast<const int4 *>(e_goff + ECH * ch + 4 * v4);
+                        go[4 * v4] = x.x; go[4 * v4 + 1] = x.y; go[4 * v4 + 2] = x.z; go[4 * v4 + 3] = x.w;
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < ECH; ++jj) sFg[jj * 129 + s_sinv[go[jj] + row]] = v[jj];
+                }
+                named_bar_sync(bar_id, 128);
                 if (a < n3) {
-                    const int cend = min(32, nc - 32 * ch);
-                    for (int j = 0; j < cend; ++j) {
-                        const int2 r = __ldg(rec + col0 + 32 * ch + j);
-                        const int tgt = rec_tgt(r.y);
-                        const int g = rec_g(r.y);
-                        if (tgt != cur) {
+                    float x[ECH];
+                    int tg[ECH];
+#pragma unroll
+                    for (int jj = 0; jj < ECH; ++jj) x[jj] = sFg[jj * 129 + a];
+#pragma unroll
+                    for (int v4 = 0; v4 < ECH / 4; ++v4) {
+                        const int4 y = *reinterpret_cast<const int4 *>(e_tgt + ECH * ch + 4 * v4);
+                        tg[4 * v4] = y.x; tg[4 * v4 + 1] = y.y; tg[4 * v4 + 2] = y.z; tg[4 * v4 + 3] = y.w;
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < ECH; ++jj) {
+                        if (tg[jj] < 0) continue;   // dead column of a ragged tile
+                        if (tg[jj] != cur) {
                             if (cur >= 0) {
                                 if (out_f64) atomicAdd(out_f64 + (size_t)cur * n3 + a, (double)acc * (double)scale);
                                 else atomicAdd(out_f32 + (size_t)cur * n3 + a, acc * scale);
                             }
                             acc = 0.0f;
-                            cur = tgt;
+                            cur = tg[jj];
                         }
-                        acc += sF[j * 129 + __ldg(sg_base + g * n3 + a)];
+                        acc += x[jj];
                     }
                 }
-                named_bar_sync(1, 128);
+                named_bar_sync(bar_id, 128);
             }
         }
         if (a < n3 && cur >= 0) {
@@ -541,16 +647,44 @@ template <int KIND>
 int tc_katoms(int n3)
 {
     constexpr int E = 128 / TcTraits<KIND>::esz;
-    return (n3 + E - 1) / E;
+    int k = (n3 + E - 1) / E;
+    return k == 3 ? 4 : k;   // instantiated for 1, 2 and 4 swizzle columns
 }
 
 template <int KIND>
 size_t tc_smem_bytes(int katoms)
 {
     using Tr = TcTraits<KIND>;
+    constexpr int ECOLS = Tr::NT / 2;
+    constexpr int ECH = ECOLS < 16 ? ECOLS : 16;
     const size_t a = (size_t)katoms * 128 * 128 * Tr::nparts;
     const size_t b = 2 * (size_t)katoms * Tr::NT * 128 * Tr::nparts;
-    return 1024 + a + b + 32 * 129 * sizeof(float) + 16 * sizeof(uint64_t);
+    const size_t kpad = (size_t)katoms * (128 / Tr::esz);
+    return 1024 + a + b + 2 * ECH * 129 * sizeof(float) + 48 * kpad * sizeof(int16_t) + 3 * Tr::NT * sizeof(int2) +
+           16 * sizeof(uint64_t);
+}
+
+template <int KIND, int KATOMS>
+m2l_status launch_atoms(const m2l_ops *ops, const Buckets &b, Layout &L, int a_bytes, const float *in, void *out,
+                        int out_fp64, double scale, cudaStream_t s)
+{
+    using Tr = TcTraits<KIND>;
+    const size_t smem = tc_smem_bytes<KIND>(KATOMS);
+    if ((int)smem > max_smem_optin()) {
+        set_error("tensor-core kernel needs %zu bytes of shared memory", smem);
+        return M2L_EUNSUPPORTED;
+    }
+    auto kern = tc_apply_kernel<KIND, KATOMS>;
+    M2L_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    long grid = num_sms();
+    const long tiles_bound = (long)(b.nnz + Tr::NT - 1) / Tr::NT + 16;
+    if (grid > tiles_bound) grid = tiles_bound;
+    kern<<<(int)grid, kThreadsTC, smem, s>>>(b.rec.as<int2>(), b.class_off.as<int>(), L.a.as<uint8_t>(), a_bytes,
+                                             L.b.as<int16_t>(), in, out_fp64 ? nullptr : (float *)out,
+                                             out_fp64 ? (double *)out : nullptr, ops->n3, (float)scale,
+                                             ops->d_status);
+    M2L_LAUNCH_CHECK("tc_apply_kernel");
+    return M2L_OK;
 }
 
 template <int KIND>
@@ -582,22 +716,12 @@ m2l_status launch_kind(const m2l_ops *ops, const Buckets &b, Layout &L, const fl
         L.ready = true;
     }
     if (b.nnz == 0) return M2L_OK;
-    const size_t smem = tc_smem_bytes<KIND>(katoms);
-    if ((int)smem > max_smem_optin()) {
-        set_error("tensor-core kernel needs %zu bytes of shared memory", smem);
-        return M2L_EUNSUPPORTED;
-    }
-    auto kern = tc_apply_kernel<KIND>;
-    M2L_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    long grid = num_sms();
-    const long tiles_bound = (long)(b.nnz + Tr::NT - 1) / Tr::NT + 16;
-    if (grid > tiles_bound) grid = tiles_bound;
-    kern<<<(int)grid, kThreadsTC, smem, s>>>(b.rec.as<int2>(), b.class_off.as<int>(), L.a.as<uint8_t>(), a_bytes,
-                                             ops->sigma.as<int16_t>(), L.b.as<int16_t>(), in,
-                                             out_fp64 ? nullptr : (float *)out, out_fp64 ? (double *)out : nullptr,
-                                             n3, katoms, (float)scale, ops->d_status);
-    M2L_LAUNCH_CHECK("tc_apply_kernel");
-    return M2L_OK;
+    if (katoms == 1) return launch_atoms<KIND, 1>(ops, b, L, a_bytes, in, out, out_fp64, scale, s);
+    if (katoms == 2) return launch_atoms<KIND, 2>(ops, b, L, a_bytes, in, out, out_fp64, scale, s);
+    if constexpr (KIND != TC_BF16X3)   // bf16 rows hold 64 nodes: ell <= 5 needs at most two columns
+        return launch_atoms<KIND, 4>(ops, b, L, a_bytes, in, out, out_fp64, scale, s);
+    set_error("no tensor-core configuration for %d swizzle columns", katoms);
+    return M2L_EUNSUPPORTED;
 }
 
 }  // namespace
