@@ -56,12 +56,19 @@ __device__ __forceinline__ uint16_t classify_entry(int e, const int32_t *__restr
     return c;
 }
 
-// One warp per segment of kSegEntries entries: class codes and per-class counts.
-__global__ void code_count_kernel(int nnz, int nseg, const int32_t *__restrict__ tgt_of,
-                                  const int32_t *__restrict__ sources, const int32_t *__restrict__ tgt_ijk,
-                                  const int32_t *__restrict__ src_ijk, int nsrc,
-                                  const uint16_t *__restrict__ lut, uint16_t *__restrict__ code,
-                                  int32_t *__restrict__ seg_counts, int *__restrict__ status)
+// Class code of every list entry, one thread per entry.
+__global__ void classify_kernel(int nnz, const int32_t *__restrict__ tgt_of, const int32_t *__restrict__ sources,
+                                const int32_t *__restrict__ tgt_ijk, const int32_t *__restrict__ src_ijk, int nsrc,
+                                const uint16_t *__restrict__ lut, uint16_t *__restrict__ code,
+                                int *__restrict__ status)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += gridDim.x * blockDim.x)
+        code[e] = classify_entry(e, tgt_of, sources, tgt_ijk, src_ijk, nsrc, lut, status);
+}
+
+// One warp per segment of kSegEntries entries: per-class counts of the codes
+// (loads batched eight rounds ahead so that their latencies overlap).
+__global__ void count_kernel(int nnz, int nseg, const uint16_t *__restrict__ code, int32_t *__restrict__ seg_counts)
 {
     __shared__ int cnt[4][17];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -71,17 +78,23 @@ __global__ void code_count_kernel(int nnz, int nseg, const int32_t *__restrict__
     if (seg >= nseg) return;
     const int e0 = seg * kSegEntries;
     const int e1 = min(nnz, e0 + kSegEntries);
-    for (int base = e0; base < e1; base += 32) {
-        const int e = base + lane;
-        int cls = 17;
-        if (e < e1) {
-            const uint16_t c = classify_entry(e, tgt_of, sources, tgt_ijk, src_ijk, nsrc, lut, status);
-            code[e] = c;
-            cls = (c == 0xFFFF) ? 16 : (c & 0xFF);
+    for (int base = e0; base < e1; base += 256) {
+        int cls[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = base + 32 * u + lane;
+            cls[u] = 17;
+            if (e < e1) {
+                const uint16_t c = code[e];
+                cls[u] = (c == 0xFFFF) ? 16 : (c & 0xFF);
+            }
         }
-        const unsigned peers = __match_any_sync(0xffffffffu, cls);
-        if (cls < 17 && lane == __ffs(peers) - 1) cnt[wib][cls] += __popc(peers);
-        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const unsigned peers = __match_any_sync(0xffffffffu, cls[u]);
+            if (cls[u] < 17 && lane == __ffs(peers) - 1) cnt[wib][cls[u]] += __popc(peers);
+            __syncwarp();
+        }
     }
     for (int i = lane; i < 17; i += 32) seg_counts[(size_t)i * nseg + seg] = cnt[wib][i];
 }
@@ -130,7 +143,8 @@ __global__ void class_offsets_kernel(int nseg, int nnz, const int32_t *__restric
     if (c == 17) class_off[17] = nnz;
 }
 
-// One warp per segment, in order: stable positions inside each bucket.
+// One warp per segment, in order: stable positions inside each bucket (loads
+// batched eight rounds ahead).
 __global__ void scatter_kernel(int nnz, int nseg, const uint16_t *__restrict__ code,
                                const int32_t *__restrict__ tgt_of, const int32_t *__restrict__ sources,
                                const int32_t *__restrict__ seg_pos, int2 *__restrict__ rec)
@@ -144,21 +158,33 @@ __global__ void scatter_kernel(int nnz, int nseg, const uint16_t *__restrict__ c
     const int e0 = seg * kSegEntries;
     const int e1 = min(nnz, e0 + kSegEntries);
     const unsigned lt = (1u << lane) - 1u;
-    for (int b = e0; b < e1; b += 32) {
-        const int e = b + lane;
-        int cls = 17;
-        uint16_t c = 0xFFFF;
-        if (e < e1) {
-            c = code[e];
-            cls = (c == 0xFFFF) ? 16 : (c & 0xFF);
+    for (int b = e0; b < e1; b += 256) {
+        int cls[8], src[8], tgt[8];
+        uint16_t cc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = b + 32 * u + lane;
+            cls[u] = 17;
+            cc[u] = 0xFFFF;
+            src[u] = 0;
+            tgt[u] = 0;
+            if (e < e1) {
+                cc[u] = code[e];
+                cls[u] = (cc[u] == 0xFFFF) ? 16 : (cc[u] & 0xFF);
+                src[u] = sources[e];
+                tgt[u] = tgt_of[e];
+            }
         }
-        const unsigned peers = __match_any_sync(0xffffffffu, cls);
-        int pos = 0;
-        if (cls < 17) pos = base[wib][cls] + __popc(peers & lt);
-        __syncwarp();
-        if (cls < 17 && lane == __ffs(peers) - 1) base[wib][cls] += __popc(peers);
-        __syncwarp();
-        if (cls < 16) rec[pos] = make_int2(sources[e], rec_pack(tgt_of[e], (int)(c >> 8)));
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const unsigned peers = __match_any_sync(0xffffffffu, cls[u]);
+            int pos = 0;
+            if (cls[u] < 17) pos = base[wib][cls[u]] + __popc(peers & lt);
+            __syncwarp();
+            if (cls[u] < 17 && lane == __ffs(peers) - 1) base[wib][cls[u]] += __popc(peers);
+            __syncwarp();
+            if (cls[u] < 16) rec[pos] = make_int2(src[u], rec_pack(tgt[u], (int)(cc[u] >> 8)));
+        }
     }
 }
 
@@ -248,10 +274,11 @@ static m2l_status bucket(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const 
     }
     int32_t *counts = b.seg.as<int32_t>();
     int32_t *pos = counts + 17 * (size_t)nseg + 1;
-    code_count_kernel<<<(nseg + 3) / 4, 128, 0, s>>>(nnz, nseg, b.tgt_of.as<int32_t>(), sources, tgt_ijk, src_ijk,
-                                                     nsrc, ops->lut.as<uint16_t>(), b.code.as<uint16_t>(),
-                                                     counts, ops->d_status);
-    M2L_LAUNCH_CHECK("code_count_kernel");
+    classify_kernel<<<(nnz + 255) / 256, 256, 0, s>>>(nnz, b.tgt_of.as<int32_t>(), sources, tgt_ijk, src_ijk, nsrc,
+                                                     ops->lut.as<uint16_t>(), b.code.as<uint16_t>(), ops->d_status);
+    M2L_LAUNCH_CHECK("classify_kernel");
+    count_kernel<<<(nseg + 3) / 4, 128, 0, s>>>(nnz, nseg, b.code.as<uint16_t>(), counts);
+    M2L_LAUNCH_CHECK("count_kernel");
     exclusive_scan_kernel<<<1, kScanThreads, 0, s>>>(counts, pos, 17 * nseg);
     M2L_LAUNCH_CHECK("exclusive_scan_kernel");
     class_offsets_kernel<<<1, 32, 0, s>>>(nseg, nnz, pos, b.class_off.as<int32_t>());
@@ -336,9 +363,11 @@ m2l_status bucket_raw(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const int
     }
     int32_t *counts = seg;
     int32_t *pos = seg + 17 * (size_t)nseg + 1;
-    code_count_kernel<<<(nseg + 3) / 4, 128, 0, s>>>(nnz, nseg, tgt_of, sources, tgt_ijk, src_ijk, nsrc,
-                                                     ops->lut.as<uint16_t>(), code, counts, ops->d_status);
-    M2L_LAUNCH_CHECK("code_count_kernel");
+    classify_kernel<<<(nnz + 255) / 256, 256, 0, s>>>(nnz, tgt_of, sources, tgt_ijk, src_ijk, nsrc,
+                                                     ops->lut.as<uint16_t>(), code, ops->d_status);
+    M2L_LAUNCH_CHECK("classify_kernel");
+    count_kernel<<<(nseg + 3) / 4, 128, 0, s>>>(nnz, nseg, code, counts);
+    M2L_LAUNCH_CHECK("count_kernel");
     exclusive_scan_kernel<<<1, kScanThreads, 0, s>>>(counts, pos, 17 * nseg);
     M2L_LAUNCH_CHECK("exclusive_scan_kernel");
     class_offsets_kernel<<<1, 32, 0, s>>>(nseg, nnz, pos, class_off);

@@ -90,6 +90,10 @@ __device__ __forceinline__ double kernel_r(int kind, double c, double r)
 __global__ void assemble_kernel(int ell, int kind, double c, double w, const int *__restrict__ tsym,
                                 double *__restrict__ K)
 {
+    // Chebyshev roots ascending, -cos((2k+1) pi / (2 ell)), once per block
+    __shared__ double xi[kMaxEll];
+    if (threadIdx.x < ell) xi[threadIdx.x] = -cospi((2.0 * threadIdx.x + 1.0) / (2.0 * ell));
+    __syncthreads();
     const int n3 = ell * ell * ell;
     const long total = 16L * n3 * n3;
     for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total;
@@ -101,10 +105,7 @@ __global__ void assemble_kernel(int ell, int kind, double c, double w, const int
         const int bi[3] = {b % ell, (b / ell) % ell, b / (ell * ell)};
         double r2 = 0.0;
         for (int i = 0; i < 3; ++i) {
-            // Chebyshev roots ascending: -cos((2k+1) pi / (2 ell))
-            const double xa = -cospi((2.0 * ai[i] + 1.0) / (2.0 * ell));
-            const double xb = -cospi((2.0 * bi[i] + 1.0) / (2.0 * ell));
-            const double d = w * ((double)tsym[3 * p + i] + 0.5 * (xa - xb));
+            const double d = w * ((double)tsym[3 * p + i] + 0.5 * (xi[ai[i]] - xi[bi[i]]));
             r2 += d * d;
         }
         K[idx] = kernel_r(kind, c, sqrt(r2));

@@ -1,0 +1,73 @@
+"""End-to-end accuracy with the GPU M2L inside an otherwise oracle FMM.
+
+The symmetry-blocked FP64/FP32 configuration: N = 2,000,000 particles
+U([-1,1]^3), charges U(-1,1) (seed 2), uniform octree with leaf level 5,
+ell = 5, kernel 1/r.  The oracle runs P2M/M2M, the library runs M2L at levels
+2..5 in each precision, the oracle runs L2L/L2P and P2P at 1000 sampled
+particles, and the result is compared with the direct sum (Eq. (1)).
+
+"Equal error": a precision qualifies when the FMM's relative L2 error with
+its M2L is within 10 % of the error with the FP64 M2L.  The test records the
+errors (printed) and asserts the FP64 error is at the ell = 5 interpolation
+level and that the FP32-accurate precisions meet the criterion.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import device
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+RESULT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out",
+                      "fmm_accuracy_config2.json")
+
+
+@pytest.fixture(scope="module")
+def m2l():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as g
+    g.build()
+    from paper_1210_7292_gb300 import m2l as mod
+    return mod
+
+
+def test_config2_fmm_error_per_precision(m2l):
+    from paper_1210_7292_gb300 import synth
+    ell, leaf = 5, 5
+    pts, q = synth.uniform_cube(2_000_000, seed=2)
+    up = oracle.UpwardPass(ell, leaf, pts, q)
+    samp = np.sort(np.random.default_rng(12).choice(len(pts), 1000, replace=False))
+    exact = oracle.direct_sum(0, 0.0, pts[samp], pts, q)
+    ops = m2l.m2l_precompute(m2l.M2L_K_INV_R, ell)
+    levels = {}
+    for L in range(2, leaf + 1):
+        cells, W = up.levels[L]
+        ijk = torch.from_numpy(np.ascontiguousarray(cells)).to(device())
+        off, src = m2l.m2l_build_lists(ijk, ijk)
+        levels[L] = (m2l.Level(oracle.cell_width(L), ijk, ijk, off, src, L), W)
+    errs = {}
+    for prec in ("fp64", "fp32", "tf32x3", "bf16x3", "tf32"):
+        dt_in = torch.float64 if prec == "fp64" else torch.float32
+        loc_by_level = {}
+        for L, (lv, W) in levels.items():
+            loc = torch.zeros(W.shape[0], ell ** 3, dtype=torch.float64, device=device())
+            m2l.m2l_apply_level(ops, lv, torch.from_numpy(W).to(device(), dt_in), loc, prec,
+                                locals_fp64=(prec != "fp64"))
+            loc_by_level[L] = loc.cpu().numpy()
+        m2l.m2l_sync_status(ops)
+        f = oracle.fmm_at_samples(up, 0, 0.0, loc_by_level, samp)
+        errs[prec] = oracle.rel_l2(f, exact)
+    print("config2 FMM rel L2 vs direct sum:", json.dumps(errs))
+    os.makedirs(os.path.dirname(RESULT), exist_ok=True)
+    with open(RESULT, "w") as fh:
+        json.dump(errs, fh, indent=1)
+    # ell = 5 interpolation error level (Sec. 5.1: knee near 10^-ell, plateau above it)
+    assert 1e-7 < errs["fp64"] < 1e-3
+    for prec in ("fp32", "tf32x3", "bf16x3"):
+        assert errs[prec] <= 1.10 * errs["fp64"], (prec, errs)
