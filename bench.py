@@ -152,6 +152,8 @@ def max_over_ranks(world, value, device):
         return value
     import torch
     import torch.distributed as dist
+    if dist.get_backend() == "gloo":
+        device = torch.device("cpu")
     t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
