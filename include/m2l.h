@@ -198,12 +198,35 @@ m2l_status m2l_plan_apply(const m2l_plan *plan, const void *in_vectors, void *ou
 m2l_status m2l_plan_query(const m2l_plan *plan, int64_t *counts16, int32_t *records, int64_t *nvalid);
 void m2l_plan_free(m2l_plan *plan);
 
-/* Batched apply: nbatch independent (ops, level) problems in one persistent
- * launch per precision family.  All ops must share one ell; in[i], out[i]
- * follow the types of m2l_apply_level.  Classification runs per problem. */
+/* Batched apply: nbatch independent (ops, level) problems.  For M2L_FP32 and
+ * M2L_FP64 the problems are classified (one plan each) and then applied by ONE
+ * persistent launch (m2l_batch_create/run/free inside the call; the call
+ * synchronises `stream` and allocates its plans -- create an m2l_batch once for
+ * repeated or graph-captured use).  Tensor-core precisions apply the problems
+ * one launch each.  in[i], out[i] follow the types of m2l_apply_level. */
 m2l_status m2l_apply_batch(const m2l_ops *const *ops, const m2l_level *levels,
                            const void *const *multipoles, void *const *locals, int nbatch,
                            int precision, int locals_fp64, void *stream);
+
+/* Persistent batches (the batched-trees workload): a fixed set of planned
+ * translations -- any mix of trees, levels and orders ell <= 7 -- run by ONE
+ * persistent kernel launch over a global tile queue.  precision: M2L_FP32 or
+ * M2L_FP64 (CUDA-core products; out_fp64 selects double outputs for FP32).
+ * in[i], out[i]: device vectors of plan i (types as m2l_plan_apply).
+ * Creation reads the plans' bucket sizes (synchronises `stream`), picks the
+ * tile width with a built-in autotuner (each candidate timed on scratch
+ * outputs; the choice is cached per precision, padded order and interaction
+ * count), and uploads the descriptor table.  m2l_batch_run allocates nothing
+ * and issues one kernel launch, so it may be captured in a CUDA graph; the
+ * plans and vectors must outlive the batch.  Full-rank operators only. */
+typedef struct m2l_batch m2l_batch;
+m2l_status m2l_batch_create(const m2l_plan *const *plans, int nbatch, const void *const *in, void *const *out,
+                            int precision, int out_fp64, void *stream, m2l_batch **out_batch);
+m2l_status m2l_batch_run(const m2l_batch *batch, void *stream);
+/* tile_width: columns per tile chosen by the autotuner; tiles: tiles per run;
+ * tuned_ms: the autotuner's best time (0 when taken from its cache). */
+m2l_status m2l_batch_info(const m2l_batch *batch, int *tile_width, int64_t *tiles, double *tuned_ms);
+void m2l_batch_free(m2l_batch *batch);
 
 /* ---------------------------------------------------------------------
  * Interaction lists (Sec. 3.2, Alg. 1 for asymptotically smooth kernels):

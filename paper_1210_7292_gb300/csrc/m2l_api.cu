@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <vector>
 
 #include "m2l_internal.cuh"
 
@@ -375,11 +376,26 @@ m2l_status m2l_apply_batch(const m2l_ops *const *ops, const m2l_level *levels, c
         set_error("bad batch arguments");
         return M2L_EINVAL;
     }
-    for (int i = 0; i < nbatch; ++i) {
-        m2l_status st = m2l_apply_level(ops[i], &levels[i], multipoles[i], locals[i], precision, locals_fp64, stream);
-        if (st != M2L_OK) return st;
+    if (precision != M2L_FP32 && precision != M2L_FP64) {
+        for (int i = 0; i < nbatch; ++i) {
+            m2l_status st = m2l_apply_level(ops[i], &levels[i], multipoles[i], locals[i], precision, locals_fp64, stream);
+            if (st != M2L_OK) return st;
+        }
+        return M2L_OK;
     }
-    return M2L_OK;
+    std::vector<m2l_plan *> plans(nbatch, nullptr);
+    m2l_status st = M2L_OK;
+    for (int i = 0; i < nbatch && st == M2L_OK; ++i) st = m2l_plan_create(ops[i], &levels[i], 0, stream, &plans[i]);
+    m2l_batch *b = nullptr;
+    if (st == M2L_OK) st = m2l_batch_create(plans.data(), nbatch, multipoles, locals, precision, locals_fp64, stream, &b);
+    if (st == M2L_OK) st = m2l_batch_run(b, stream);
+    if (st == M2L_OK) {
+        cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "batched apply");
+    }
+    m2l_batch_free(b);
+    for (m2l_plan *p : plans) m2l_plan_free(p);
+    return st;
 }
 
 m2l_status m2l_sync_status(const m2l_ops *ops, void *stream)

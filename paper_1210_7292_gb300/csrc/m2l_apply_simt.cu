@@ -293,3 +293,115 @@ m2l_status launch_simt_f32_raw(const m2l_ops *ops, const int2 *rec, const int *c
 }
 
 }  // namespace m2l
+
+// ---------------------------------------------------------------------------
+// Batched apply: many (operator set, level) problems in one persistent launch.
+namespace m2l {
+
+
+namespace {
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(kThreads)
+simt_batch_kernel(const BatchDesc *__restrict__ descs, int nprob, int total_tiles)
+{
+    constexpr int KC = kc_of<T>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_base[1025];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool base_in_smem = nprob <= 1024;
+    if (base_in_smem)
+        for (int i = threadIdx.x; i < nprob; i += kThreads) s_base[i] = descs[i].tile_base;
+    __syncthreads();
+    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+        // problem owning the tile: last problem whose tile_base <= tile
+        int lo = 0, hi = nprob - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            const int b = base_in_smem ? s_base[mid] : descs[mid].tile_base;
+            if (b <= tile) lo = mid; else hi = mid - 1;
+        }
+        const BatchDesc &d = descs[lo];
+        const int lt = tile - d.tile_base;
+        int p = 0;
+        while (p < 15 && lt >= d.tile_start[p + 1]) ++p;
+        const int col0 = d.class_off[p] + (lt - d.tile_start[p]) * NT;
+        const int nc = min(NT, d.class_off[p + 1] - col0);
+        const int n3 = d.n3, kpad = d.kpad, mpad = d.mpad;
+        T *As = reinterpret_cast<T *>(smem_raw);                   // [KC][128]
+        T *Bs = As + KC * 128;                                     // [kpad][NT + 1]
+        T *Cs = Bs + (size_t)kpad * (NT + 1);                      // [NT][mpad + 1]
+        int2 *recs = reinterpret_cast<int2 *>(Cs + (size_t)NT * (mpad + 1));
+        const T *mp = static_cast<const T *>(d.in);
+        for (int c = threadIdx.x; c < NT; c += kThreads) recs[c] = (c < nc) ? d.rec[col0 + c] : make_int2(0, 0);
+        for (int idx = threadIdx.x; idx < (kpad - n3) * (NT + 1); idx += kThreads) Bs[n3 * (NT + 1) + idx] = T(0);
+        __syncthreads();
+        for (int c = warp; c < NT; c += kThreads / 32) {
+            if (c < nc) {
+                const int2 r = recs[c];
+                const T *w = mp + (size_t)r.x * n3;
+                const int16_t *sg = d.sigma + rec_g(r.y) * n3;
+                for (int b = lane; b < n3; b += 32) Bs[sg[b] * (NT + 1) + c] = w[b];
+            } else {
+                for (int b = lane; b < n3; b += 32) Bs[b * (NT + 1) + c] = T(0);
+            }
+        }
+        __syncthreads();
+        gemm_chunked<T, NT, 0>(static_cast<const T *>(d.A) + (size_t)p * kpad * mpad, mpad, kpad, n3, Bs, As, Cs,
+                               mpad + 1);
+        for (int a = threadIdx.x; a < n3; a += kThreads) {
+            T acc = T(0);
+            int cur = rec_tgt(recs[0].y);
+            for (int c = 0; c < nc; ++c) {
+                const int2 r = recs[c];
+                const int tgt = rec_tgt(r.y);
+                if (tgt != cur) {
+                    if (d.out_fp64) atomicAdd(static_cast<double *>(d.out) + (size_t)cur * n3 + a, (double)acc * d.scale);
+                    else atomicAdd(static_cast<float *>(d.out) + (size_t)cur * n3 + a, (float)(acc * (T)d.scale));
+                    acc = T(0);
+                    cur = tgt;
+                }
+                acc += Cs[c * (mpad + 1) + d.sigma[rec_g(r.y) * n3 + a]];
+            }
+            if (d.out_fp64) atomicAdd(static_cast<double *>(d.out) + (size_t)cur * n3 + a, (double)acc * d.scale);
+            else atomicAdd(static_cast<float *>(d.out) + (size_t)cur * n3 + a, (float)(acc * (T)d.scale));
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+size_t batch_smem_bytes(int fp64, int nt, int kpad_max, int mpad_max)
+{
+    const size_t esz = fp64 ? sizeof(double) : sizeof(float);
+    const size_t kc = fp64 ? 16 : 32;
+    return (kc * 128 + (size_t)kpad_max * (nt + 1) + (size_t)nt * (mpad_max + 1)) * esz + nt * sizeof(int2);
+}
+
+// One persistent launch over all problems of the table.
+m2l_status launch_simt_batch(const BatchDesc *descs, int nprob, int total_tiles, int fp64, int nt, int kpad_max,
+                             int mpad_max, cudaStream_t s)
+{
+    if (total_tiles == 0) return M2L_OK;
+    const size_t smem = batch_smem_bytes(fp64, nt, kpad_max, mpad_max);
+    if ((int)smem > max_smem_optin()) {
+        set_error("batched SIMT kernel needs %zu bytes of shared memory", smem);
+        return M2L_EUNSUPPORTED;
+    }
+    void (*kern)(const BatchDesc *, int, int);
+    if (fp64) kern = simt_batch_kernel<double, 32>;
+    else if (nt == 64) kern = simt_batch_kernel<float, 64>;
+    else kern = simt_batch_kernel<float, 32>;
+    M2L_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    M2L_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+    if (per_sm < 1) per_sm = 1;
+    long grid = (long)num_sms() * per_sm;
+    if (grid > total_tiles) grid = total_tiles;
+    kern<<<(int)grid, kThreads, smem, s>>>(descs, nprob, total_tiles);
+    M2L_LAUNCH_CHECK("simt_batch_kernel");
+    return M2L_OK;
+}
+
+}  // namespace m2l

@@ -142,4 +142,19 @@ m2l_status launch_tc(const m2l_ops *ops, const Buckets &b, const void *in, void 
 int num_sms();
 int max_smem_optin();
 
+// One problem of a batched persistent launch (host-built, copied to the device).
+struct BatchDesc {
+    const int2 *rec;          // bucketed records of the problem
+    const void *A;            // transposed operator layout [16][kpad][mpad] (float or double)
+    const int16_t *sigma;     // permutation tables [48][n3]
+    const void *in;           // input vectors [n_in][n3]
+    void *out;                // output vectors [n_out][n3] (accumulated)
+    double scale;             // w^degree for homogeneous kernels, else 1
+    int n3, kpad, mpad, out_fp64;
+    int class_off[17];        // bucket offsets (from the plan)
+    int tile_start[17];       // first tile of each bucket within the problem
+    int tile_base;            // first global tile of the problem
+    int pad_;
+};
+
 }  // namespace m2l

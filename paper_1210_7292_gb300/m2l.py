@@ -68,6 +68,9 @@ def lib():
             "m2l_apply_batch": [P, ctypes.POINTER(m2l_level), P, P, I, I, I, P],
             "m2l_build_lists": [I, P, I, P, P, P, P, P],
             "m2l_apply_level_noalloc": [P, ctypes.POINTER(m2l_level), P, P, P],
+            "m2l_batch_create": [P, I, P, P, I, I, P, ctypes.POINTER(P)],
+            "m2l_batch_run": [P, P],
+            "m2l_batch_info": [P, P, P, P],
             "m2l_sync_status": [P, P],
         }
         for name, args in sig.items():
@@ -78,6 +81,8 @@ def lib():
         L.m2l_ops_free.restype = None
         L.m2l_plan_free.argtypes = [P]
         L.m2l_plan_free.restype = None
+        L.m2l_batch_free.argtypes = [P]
+        L.m2l_batch_free.restype = None
         L.m2l_last_error.argtypes = []
         L.m2l_last_error.restype = ctypes.c_char_p
         L.m2l_launch_count.argtypes = []
@@ -283,6 +288,44 @@ def m2l_apply_batch(ops_list, levels, multipoles, locals_, precision="fp32", loc
     arr_out = (ctypes.c_void_p * n)(*[_dev_ptr(t, tout, "locals").value for t in locals_])
     _check("m2l_apply_batch", lib().m2l_apply_batch(arr_ops, arr_lv, arr_in, arr_out, n, p, int(bool(locals_fp64)),
                                                     _stream_ptr(stream)))
+
+
+class Batch:
+    """Owner of an m2l_batch; keeps its plans and vectors alive."""
+
+    def __init__(self, handle, plans, ins, outs):
+        self.handle, self.plans, self.ins, self.outs = handle, plans, ins, outs
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.m2l_batch_free(h)
+
+
+def m2l_batch_create(plans, ins, outs, precision="fp32", out_fp64=False, stream=None) -> Batch:
+    """One persistent launch over a fixed set of planned translations (FP32/FP64)."""
+    n = len(plans)
+    p, tin, tout = _vec_dtypes(precision, out_fp64)
+    for pl, a, b in zip(plans, ins, outs):
+        _check_shapes(pl.ops, a, b, pl.n_in, pl.n_out)
+    arr_pl = (ctypes.c_void_p * n)(*[pl.handle.value for pl in plans])
+    arr_in = (ctypes.c_void_p * n)(*[_dev_ptr(t, tin, "input vectors").value for t in ins])
+    arr_out = (ctypes.c_void_p * n)(*[_dev_ptr(t, tout, "output vectors").value for t in outs])
+    h = ctypes.c_void_p()
+    _check("m2l_batch_create", lib().m2l_batch_create(arr_pl, n, arr_in, arr_out, p, int(bool(out_fp64)),
+                                                      _stream_ptr(stream), ctypes.byref(h)))
+    return Batch(h, list(plans), list(ins), list(outs))
+
+
+def m2l_batch_run(batch: Batch, stream=None):
+    _check("m2l_batch_run", lib().m2l_batch_run(batch.handle, _stream_ptr(stream)))
+
+
+def m2l_batch_info(batch: Batch):
+    nt, tiles, ms = ctypes.c_int(), ctypes.c_int64(), ctypes.c_double()
+    _check("m2l_batch_info", lib().m2l_batch_info(batch.handle, ctypes.byref(nt), ctypes.byref(tiles),
+                                                  ctypes.byref(ms)))
+    return {"tile_width": nt.value, "tiles": tiles.value, "tuned_ms": ms.value}
 
 
 def m2l_build_lists(tgt_ijk, src_ijk, stream=None):
