@@ -569,10 +569,18 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
                         const int4 y = *reinterpret_cast<const int4 *>(e_tgt + ECH * ch + 4 * v4);
                         tg[4 * v4] = y.x; tg[4 * v4 + 1] = y.y; tg[4 * v4 + 2] = y.z; tg[4 * v4 + 3] = y.w;
                     }
+                    // columns where a new target run starts, found without branches (a dead
+                    // column of a ragged tile holds zeros and starts no run)
+                    unsigned bm = 0u;
+                    int prev = cur;
 #pragma unroll
                     for (int jj = 0; jj < ECH; ++jj) {
-                        if (tg[jj] < 0) continue;   // dead column of a ragged tile
-                        if (tg[jj] != cur) {
+                        bm |= ((tg[jj] >= 0 && tg[jj] != prev) ? 1u : 0u) << jj;
+                        prev = tg[jj] >= 0 ? tg[jj] : prev;
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < ECH; ++jj) {
+                        if (bm & (1u << jj)) {
                             if (cur >= 0) {
                                 if (out_f64) atomicAdd(out_f64 + (size_t)cur * n3 + a, (double)acc * (double)scale);
                                 else atomicAdd(out_f32 + (size_t)cur * n3 + a, acc * scale);
