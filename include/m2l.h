@@ -264,6 +264,15 @@ m2l_status m2l_build_lists(int ncells_tgt, const int32_t *tgt_ijk, int ncells_sr
 m2l_status m2l_apply_level_noalloc(const m2l_ops *ops, const m2l_level *level, const float *multipoles,
                                    float *locals, void *stream);
 
+/* Test switches of an ops object (0 = none).  M2L_DEBUG_STALL_PRODUCER makes
+ * every CTA of the tensor-core apply withhold its first stage signal: the
+ * MMA warp's bounded wait (about two seconds) runs out, the CTA drains its
+ * own asynchronous copies, frees its tensor memory and returns, and the next
+ * m2l_sync_status reports M2L_ETIMEOUT.  Used to test failure detection
+ * without faulting the GPU; the results of such a call are incomplete. */
+#define M2L_DEBUG_STALL_PRODUCER 1
+m2l_status m2l_ops_set_debug(m2l_ops *ops, int flags);
+
 /* ---------------------------------------------------------------------
  * Synchronises `stream`, then returns and clears the device status word of
  * ops (M2L_OK, M2L_EINVAL for list entries that were skipped, M2L_ETIMEOUT). */

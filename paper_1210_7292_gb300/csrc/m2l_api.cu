@@ -398,6 +398,13 @@ m2l_status m2l_apply_batch(const m2l_ops *const *ops, const m2l_level *levels, c
     return st;
 }
 
+m2l_status m2l_ops_set_debug(m2l_ops *ops, int flags)
+{
+    if (!ops) { set_error("null ops"); return M2L_EINVAL; }
+    ops->debug_flags = flags;
+    return M2L_OK;
+}
+
 m2l_status m2l_sync_status(const m2l_ops *ops, void *stream)
 {
     if (!ops) { set_error("null ops"); return M2L_EINVAL; }

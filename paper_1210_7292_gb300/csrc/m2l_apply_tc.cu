@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
                 const uint8_t *__restrict__ a_img, int a_bytes, const int16_t *__restrict__ sigma_inv,
                 const float *__restrict__ mp, float *__restrict__ out_f32, double *__restrict__ out_f64, int n3,
-                float scale, int *status)
+                float scale, int *status, int stall_first_stage)
 {
     using Tr = TcTraits<KIND>;
     constexpr int NT = Tr::NT;
@@ -443,7 +443,9 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
                 }
             }
             fence_proxy_async();
-            mbar_arrive(full + s);
+            // stall_first_stage (a test switch) withholds the first stage's signal, so the
+            // MMA warp's bounded wait runs out and the CTA takes its abort path
+            if (!(stall_first_stage && i == 0)) mbar_arrive(full + s);
         }
         // an operator image still in flight must land before the CTA exits
         if (ptid == 0 && a_loads > 0) mbar_wait_drain(afull, (a_loads - 1) & 1, status);
@@ -690,7 +692,7 @@ m2l_status launch_atoms(const m2l_ops *ops, const Buckets &b, Layout &L, int a_b
     kern<<<(int)grid, kThreadsTC, smem, s>>>(b.rec.as<int2>(), b.class_off.as<int>(), L.a.as<uint8_t>(), a_bytes,
                                              L.b.as<int16_t>(), in, out_fp64 ? nullptr : (float *)out,
                                              out_fp64 ? (double *)out : nullptr, ops->n3, (float)scale,
-                                             ops->d_status);
+                                             ops->d_status, (ops->debug_flags & M2L_DEBUG_STALL_PRODUCER) ? 1 : 0);
     M2L_LAUNCH_CHECK("tc_apply_kernel");
     return M2L_OK;
 }

@@ -108,6 +108,7 @@ struct m2l_ops {
     mutable m2l::Buckets ws;  // workspace of m2l_apply_level
     mutable double ws_scale = 1.0;  // scale of the level last classified into ws
     int *d_status = nullptr;  // device status word
+    int debug_flags = 0;      // M2L_DEBUG_* test switches
 };
 
 struct m2l_plan {

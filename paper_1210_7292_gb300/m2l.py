@@ -72,6 +72,7 @@ def lib():
             "m2l_batch_run": [P, P],
             "m2l_batch_info": [P, P, P, P],
             "m2l_sync_status": [P, P],
+            "m2l_ops_set_debug": [P, I],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -355,6 +356,13 @@ def m2l_apply_level_noalloc(ops: Ops, level: Level, multipoles, locals_, stream=
 
 def m2l_sync_status(ops: Ops, stream=None):
     _check("m2l_sync_status", lib().m2l_sync_status(ops.handle, _stream_ptr(stream)))
+
+
+M2L_DEBUG_STALL_PRODUCER = 1
+
+
+def m2l_ops_set_debug(ops: Ops, flags: int):
+    _check("m2l_ops_set_debug", lib().m2l_ops_set_debug(ops.handle, int(flags)))
 
 
 def m2l_last_error() -> str:
