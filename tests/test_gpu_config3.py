@@ -6,8 +6,8 @@ per-operator truncated SVD at eps = 1e-7 (Eq. (20)).
 Level 6 is applied with the low-rank and the full-rank operators in FP64 and
 FP32 on the CUDA cores and compared on sampled targets with the oracle's
 per-pair truncated operators; the relative L2 error of each precision
-against the FP64 oracle is printed.  (The tensor-core precisions are built
-for ell <= 5 and refuse ell = 7 with M2L_EUNSUPPORTED.)"""
+against the FP64 oracle is printed; the full-rank operators also run in the
+tensor-core precisions (TF32, split BF16, split TF32 with FP32 accumulation)."""
 import numpy as np
 import pytest
 
@@ -71,8 +71,13 @@ def test_config3_level6_lowrank_and_full(m2l):
             errs[(name, prec)] = oracle.rel_l2(got, ref)
             assert errs[(name, prec)] < TOL[prec], (name, prec, errs[(name, prec)])
     print("config3 rel L2 vs FP64 oracle:", {"%s/%s" % k: "%.2e" % v for k, v in errs.items()})
-    for prec in ("tf32", "bf16x3"):
-        loc = torch.zeros(len(cells), ell ** 3, dtype=torch.float32, device=device())
-        with pytest.raises(m2l.M2LError) as ei:
-            m2l.m2l_apply_level(ops_full, lv, torch.from_numpy(w).to(device(), torch.float32), loc, prec)
-        assert ei.value.status == m2l.M2L_EUNSUPPORTED
+    # the tensor-core precisions on the full-rank operators (FP32 accumulation)
+    for prec in ("tf32", "bf16x3", "tf32x3"):
+        loc = torch.zeros(len(cells), ell ** 3, dtype=torch.float64, device=device())
+        m2l.m2l_apply_level(ops_full, lv, torch.from_numpy(w).to(device(), torch.float32), loc, prec,
+                            locals_fp64=True)
+        m2l.m2l_sync_status(ops_full)
+        errs[("full", prec)] = oracle.rel_l2(loc[idx].cpu().numpy(), ref_full)
+        assert errs[("full", prec)] < TOL[prec], (prec, errs[("full", prec)])
+    print("config3 tensor-core rel L2 vs FP64 oracle:",
+          {p: "%.2e" % errs[("full", p)] for p in ("tf32", "bf16x3", "tf32x3")})

@@ -105,12 +105,33 @@ def test_tc_level5_sampled(m2l):
         print("level5 %s rel L2 %.3e" % (p, err))
 
 
+@pytest.mark.parametrize("prec", TC)
+@pytest.mark.parametrize("ell,kind,level,keep", [(6, 2, 3, 0.6), (7, 1, 3, 0.5), (8, 0, 3, 0.15)])
+def test_tc_large_orders(m2l, prec, ell, kind, level, keep):
+    """ell = 6..8: the operator is streamed through a ring of swizzled blocks and
+    the accumulator spans two to four M tiles (ragged last tile included)."""
+    cells = pruned_cells(level, keep, seed=ell * 3 + kind)
+    rng = np.random.default_rng(ell + 7)
+    w = rng.standard_normal((len(cells), ell ** 3))
+    lv = make_level(m2l, cells, level)
+    ops = gpu_ops(m2l, ell, kind, level)
+    off, src = oracle.interaction_lists(cells, cells)
+    ref = oracle.m2l_apply(oracle_ops(ell, kind, level), cells, cells, off, src, w)
+    try:
+        got = _apply(m2l, ops, lv, w, prec)
+    except m2l.M2LError as e:
+        # the only configuration that does not fit shared memory
+        assert (ell, prec) == (8, "tf32x3") and e.status == m2l.M2L_EUNSUPPORTED
+        return
+    err = _check(got, ref, prec)
+    print("ell %d %s rel L2 %.3e" % (ell, prec, err))
+
+
 def test_tc_unsupported_requests_refused(m2l):
     cells = pruned_cells(3, 0.3, 2)
     lv = make_level(m2l, cells, 3)
-    for ell, eps in ((6, 0.0), (4, 1e-4)):
-        ops = gpu_ops(m2l, ell, 0, 3, eps=eps)
-        w = np.zeros((len(cells), ell ** 3))
-        with pytest.raises(m2l.M2LError) as ei:
-            _apply(m2l, ops, lv, w, "tf32")
-        assert ei.value.status == m2l.M2L_EUNSUPPORTED
+    ops = gpu_ops(m2l, 4, 0, 3, eps=1e-4)
+    w = np.zeros((len(cells), 64))
+    with pytest.raises(m2l.M2LError) as ei:
+        _apply(m2l, ops, lv, w, "tf32")
+    assert ei.value.status == m2l.M2L_EUNSUPPORTED
