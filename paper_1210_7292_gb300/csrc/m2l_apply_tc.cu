@@ -7,11 +7,13 @@
 //              permute them (W_p[sigma_g(b)][c] = w[b], Eq. (30)) straight into
 //              a 128-byte-swizzled K-major shared-memory panel (the UMMA B
 //              operand), rounded to TF32 or split into BF16/TF32 hi + lo;
-//              when the operator changes, one thread copies its pre-swizzled
-//              image (the UMMA A operand) with cp.async.bulk.
+//              when the operator changes, warps 0-3 (one per TMEM lane
+//              quarter) write its rows into TMEM with tcgen05.st: the UMMA A
+//              operand lives in TMEM, next to the accumulators.
 //   warp 8     allocates TMEM and issues tcgen05.mma (one thread):
-//              F_p = K_p W_p (Eq. (31)) into a double-buffered TMEM accumulator,
-//              three products hi*hi + hi*lo + lo*hi for the split precisions.
+//              F_p = K_p W_p (Eq. (31)) into one of three or four TMEM
+//              accumulators, three products hi*hi + hi*lo + lo*hi for the
+//              split precisions.
 //   warps 9-16 epilogue (two groups of four, each owning half the columns): tcgen05.ld of the accumulator, un-permutation
 //              f[a] += F_p[sigma_g(a)] (Eq. (32)) through a shared-memory
 //              transpose, sum over the consecutive columns of one target,
@@ -219,6 +221,43 @@ __device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, float (&v)[8])
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// UMMA with the A operand in TMEM (rows = lanes, K along 32-bit columns; two
+// BF16 values per column, the even K index in the low half).
+template <int KIND>
+__device__ __forceinline__ void umma_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t acc)
+{
+    if constexpr (KIND == TC_BF16X3) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(acc)
+            : "memory");
+    }
+}
+
+// 32 consecutive TMEM columns of this thread's lane <- r[0..31].
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+__host__ __device__ constexpr int tmem_alloc_cols(int n) { return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : n <= 256 ? 256 : 512; }
+
 __device__ __forceinline__ float tf32_rna(float x)
 {
     uint32_t r;
@@ -248,10 +287,17 @@ __device__ __forceinline__ void tile_info(int t, const int *tile_start, const in
     nc = min(NT, class_off[p + 1] - col0);
 }
 
+// TMEM columns of one operand part of A for KATOMS swizzle columns of K.
+template <int KIND>
+__host__ __device__ constexpr int tc_a_cols_part(int katoms)
+{
+    return katoms * (128 / TcTraits<KIND>::esz) * TcTraits<KIND>::esz / 4;
+}
+
 template <int KIND, int KATOMS>
 __global__ void __launch_bounds__(kThreadsTC, 1)
 tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
-                const uint8_t *__restrict__ a_img, int a_bytes, const int16_t *__restrict__ sigma_inv,
+                const uint32_t *__restrict__ a_img, const int16_t *__restrict__ sigma_inv,
                 const float *__restrict__ mp, float *__restrict__ out_f32, double *__restrict__ out_f64, int n3,
                 float scale, int *status, int stall_first_stage)
 {
@@ -266,7 +312,7 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
     constexpr int NPT = kProducerWarps * 32;                 // producer threads
     constexpr int NCG = NPT / CPC;                           // column stride of a producer thread
     constexpr int CPT = (NT + NCG - 1) / NCG;                // columns per producer thread
-    constexpr int A_PART = KATOMS * 128 * 128;               // one operand part of A (128 rows)
+    constexpr int A_COLS_PART = tc_a_cols_part<KIND>(KATOMS);  // TMEM columns of one part of A
     constexpr int B_PART = KATOMS * NT * 128;                // one operand part of a B stage
     constexpr int B_STAGE = B_PART * Tr::nparts;
     constexpr int ECOLS = NT / 2;                            // columns per epilogue group and tile
@@ -279,14 +325,13 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
     // access below stays a shared-memory access (an integer round trip would
     // turn them into generic ones)
     uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    uint8_t *sA = smem;                                               // a_bytes
-    uint8_t *sB = sA + a_bytes;                                       // 2 stages
+    uint8_t *sB = smem;                                               // 2 stages
     float *sF = reinterpret_cast<float *>(sB + 2 * B_STAGE);          // [2 groups][ECH][129] transposes
     int16_t *s_sinv = reinterpret_cast<int16_t *>(sF + 2 * ECH * 129);  // [48][KPAD] inverse permutations
     int2 *s_prec = reinterpret_cast<int2 *>(s_sinv + 48 * KPAD);      // [2][NT] producer records
     int2 *s_erec = s_prec + 2 * NT;                                   // [2 groups][2][ECOLS] ints: column tables
     uint64_t *bars = reinterpret_cast<uint64_t *>(s_erec + NT);
-    uint64_t *full = bars, *empty = bars + 2, *tfull = bars + 4, *tempty = bars + 8, *afull = bars + 12,
+    uint64_t *full = bars, *empty = bars + 2, *tfull = bars + 4, *tempty = bars + 8, *a_ready = bars + 12,
              *drain = bars + 13;
     __shared__ uint32_t s_tmem_base;
     __shared__ int s_abort;
@@ -294,8 +339,11 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
     __shared__ TileSched s_sched;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int NACC = 4;                      // TMEM accumulator buffers
-    constexpr int TMEM_COLS = NACC * NT;
+    // TMEM: NACC accumulators of NT columns, then the operator (nparts x A_COLS_PART columns)
+    constexpr int NACC = (4 * NT + Tr::nparts * A_COLS_PART <= 512) ? 4 : 3;
+    constexpr int A_COL0 = NACC * NT;
+    constexpr int TMEM_COLS = tmem_alloc_cols(A_COL0 + Tr::nparts * A_COLS_PART);
+    static_assert(A_COL0 + Tr::nparts * A_COLS_PART <= 512 && A_COLS_PART % 32 == 0, "TMEM budget");
 
     // inverse permutation tables sigma_g^{-1}, rows padded to KPAD with index 0
     // (padded K rows of the panel meet zero operator columns)
@@ -322,7 +370,7 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
             mbar_init(tfull + i, 1);
             mbar_init(tempty + i, kEpiWarps * 32);
         }
-        mbar_init(afull, 1);
+        mbar_init(a_ready, 128);
         mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -345,7 +393,6 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
         const int j = ptid % CPC;            // 16-byte chunk of the column this thread fills
         const int cg = ptid / CPC;           // first column of this thread
         int prev_p = -1;
-        uint32_t a_loads = 0;
         // records are fetched one tile ahead, into a register of thread c < NT
         int2 nxt = make_int2(0, 0);
         if (first < last && ptid < NT) {
@@ -358,13 +405,34 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
             int p, col0, nc;
             tile_info(t, s_tile_start, class_off, NT, p, col0, nc);
             if (p != prev_p) {
-                if (ptid == 0) {
+                // the operator changes: once the MMAs of the previous tile (the last readers
+                // of the old operator) are complete, warps 0-3 write the rows of K_p into
+                // TMEM, each warp its own lane quarter, thread ptid row ptid
+                if (ptid < 128) {
                     bool ok = true;
                     if (i > 0) ok = mbar_wait(empty + ((i - 1) & 1), ((i - 1) >> 1) & 1, abort_flag, status);
-                    if (ok) {
-                        mbar_arrive_expect_tx(afull, (uint32_t)a_bytes);
-                        bulk_g2s(sA, a_img + (size_t)p * a_bytes, (uint32_t)a_bytes, afull);
-                        ++a_loads;
+                    // tcgen05.st is warp-collective: the whole warp writes or none of it
+                    if (__all_sync(0xffffffffu, ok)) {
+                        tc_fence_after();
+#pragma unroll 1
+                        for (int part = 0; part < Tr::nparts; ++part) {
+                            const uint4 *src = reinterpret_cast<const uint4 *>(
+                                a_img + (((size_t)p * Tr::nparts + part) * 128 + ptid) * A_COLS_PART);
+#pragma unroll 1
+                            for (int c0 = 0; c0 < A_COLS_PART; c0 += 32) {
+                                uint32_t r[32];
+#pragma unroll
+                                for (int v = 0; v < 8; ++v) {
+                                    const uint4 x = __ldg(src + c0 / 4 + v);
+                                    r[4 * v] = x.x; r[4 * v + 1] = x.y; r[4 * v + 2] = x.z; r[4 * v + 3] = x.w;
+                                }
+                                tmem_st32(tmem_base + ((uint32_t)(32 * warp) << 16) +
+                                              (uint32_t)(A_COL0 + part * A_COLS_PART + c0), r);
+                            }
+                        }
+                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                        tc_fence_before();
+                        mbar_arrive(a_ready);
                     }
                 }
                 prev_p = p;
@@ -447,13 +515,11 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
             // MMA warp's bounded wait runs out and the CTA takes its abort path
             if (!(stall_first_stage && i == 0)) mbar_arrive(full + s);
         }
-        // an operator image still in flight must land before the CTA exits
-        if (ptid == 0 && a_loads > 0) mbar_wait_drain(afull, (a_loads - 1) & 1, status);
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------------------ MMA issue
         if (lane == 0) {
             const uint32_t idesc = instr_desc(Tr::fmt, NT);
-            const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sB);
+            const uint32_t a_base = tmem_base + (uint32_t)A_COL0, b_base = smem_u32(sB);
             int prev_p = -1;
             uint32_t a_loads = 0;
             bool issued = false;
@@ -463,11 +529,12 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
                 tile_info(t, s_tile_start, class_off, NT, p, col0, nc);
                 if (!mbar_wait(full + s, k & 1, abort_flag, status)) break;
                 if (p != prev_p) {
-                    if (!mbar_wait(afull, a_loads & 1, abort_flag, status)) break;
+                    if (!mbar_wait(a_ready, a_loads & 1, abort_flag, status)) break;
+                    tc_fence_after();
                     ++a_loads;
                     prev_p = p;
                 }
-                const int ab = i & (NACC - 1), ak = i / NACC;
+                const int ab = i % NACC, ak = i / NACC;
                 if (!mbar_wait(tempty + ab, (ak & 1) ^ 1, abort_flag, status)) break;
                 tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(ab * NT);
@@ -477,15 +544,15 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
                 for (int ka = 0; ka < KATOMS; ++ka) {
 #pragma unroll
                     for (int m = 0; m < MMAS_PER_ATOM; ++m) {
-                        const uint32_t koff = (uint32_t)(m * 32);
-                        const uint32_t a0 = a_base + (uint32_t)(ka * 128 * 128) + koff;
-                        const uint32_t b0 = bst + (uint32_t)(ka * NT * 128) + koff;
-                        umma<KIND>(d, smem_desc(a0), smem_desc(b0), idesc, accum);
+                        // 32 bytes of K per MMA: 8 TMEM columns of A, 32 bytes into the swizzled B row
+                        const uint32_t a0 = a_base + (uint32_t)(ka * 32 + m * 8);
+                        const uint32_t b0 = bst + (uint32_t)(ka * NT * 128) + (uint32_t)(m * 32);
+                        umma_ta<KIND>(d, a0, smem_desc(b0), idesc, accum);
                         accum = 1;
                         if constexpr (Tr::nprod == 3) {
                             // hi*lo and lo*hi into the same accumulator
-                            umma<KIND>(d, smem_desc(a0), smem_desc(b0 + (uint32_t)B_PART), idesc, 1);
-                            umma<KIND>(d, smem_desc(a0 + (uint32_t)A_PART), smem_desc(b0), idesc, 1);
+                            umma_ta<KIND>(d, a0, smem_desc(b0 + (uint32_t)B_PART), idesc, 1);
+                            umma_ta<KIND>(d, a0 + (uint32_t)A_COLS_PART, smem_desc(b0), idesc, 1);
                         }
                     }
                 }
@@ -523,7 +590,7 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
             if (a < nc0 - gc0) nxt = __ldg(rec + c00 + gc0 + a).y;
         }
         for (int t = first; t < last; ++t) {
-            const int i = t - first, ab = i & (NACC - 1), ak = i / NACC;
+            const int i = t - first, ab = i % NACC, ak = i / NACC;
             int p, col0, nc;
             tile_info(t, s_tile_start, class_off, NT, p, col0, nc);
             const int gnc = min(ECOLS, nc - gc0);         // live columns of this group (may be <= 0)
@@ -965,37 +1032,36 @@ __global__ void sigma_inverse_kernel(int n3, const int16_t *__restrict__ sigma, 
     }
 }
 
-// Pre-swizzled A images: per operator p, nparts x katoms swizzle columns of
-// 128 rows x 128 bytes; row a = output node (zero beyond n3), K = source node.
+// Operator images for TMEM: per operator p and operand part, 128 rows of
+// tc_a_cols_part 32-bit columns (row a = output node, zero beyond n3; column j
+// = source node j for TF32, source nodes 2j and 2j + 1 for BF16, the even one in
+// the low half), the split precisions storing hi and lo as two parts.
 template <int KIND>
-__global__ void a_image_kernel(int n3, int katoms, const double *__restrict__ K, uint8_t *__restrict__ img)
+__global__ void a_tmem_image_kernel(int n3, int cols_part, const double *__restrict__ K, uint32_t *__restrict__ img)
 {
     using Tr = TcTraits<KIND>;
-    constexpr int E = 128 / Tr::esz;
-    const int part_bytes = katoms * 128 * 128;
     const int p = blockIdx.y;
-    uint8_t *base = img + (size_t)p * part_bytes * Tr::nparts;
-    const int kpad = katoms * E;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 128 * kpad; idx += gridDim.x * blockDim.x) {
-        const int row = idx / kpad, kk = idx % kpad;
-        const double x = (row < n3 && kk < n3) ? K[((size_t)p * n3 + row) * n3 + kk] : 0.0;
-        const int ka = kk / E, e = kk % E;
-        const int chunk = e / (16 / Tr::esz), within = e % (16 / Tr::esz);
-        const uint32_t off = (uint32_t)ka * 16384u +
-                             (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + (((chunk ^ (row & 7))) << 4)) +
-                             (uint32_t)(within * Tr::esz);
+    uint32_t *base = img + (size_t)p * Tr::nparts * 128 * cols_part;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 128 * cols_part; idx += gridDim.x * blockDim.x) {
+        const int row = idx / cols_part, col = idx % cols_part;
         if constexpr (KIND == TC_BF16X3) {
-            const __nv_bfloat16 h = __double2bfloat16(x);
-            const __nv_bfloat16 l = __double2bfloat16(x - (double)__bfloat162float(h));
-            *reinterpret_cast<__nv_bfloat16 *>(base + off) = h;
-            *reinterpret_cast<__nv_bfloat16 *>(base + part_bytes + off) = l;
-        } else if constexpr (KIND == TC_TF32) {
-            *reinterpret_cast<float *>(base + off) = tf32_rna((float)x);
+            uint32_t hi = 0, lo = 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int kk = 2 * col + h;
+                const double x = (row < n3 && kk < n3) ? K[((size_t)p * n3 + row) * n3 + kk] : 0.0;
+                const __nv_bfloat16 bh = __double2bfloat16(x);
+                const __nv_bfloat16 bl = __double2bfloat16(x - (double)__bfloat162float(bh));
+                hi |= (uint32_t)__bfloat16_as_ushort(bh) << (16 * h);
+                lo |= (uint32_t)__bfloat16_as_ushort(bl) << (16 * h);
+            }
+            base[idx] = hi;
+            base[128 * cols_part + idx] = lo;
         } else {
+            const double x = (row < n3 && col < n3) ? K[((size_t)p * n3 + row) * n3 + col] : 0.0;
             const float h = tf32_rna((float)x);
-            const float l = tf32_rna((float)(x - (double)h));
-            *reinterpret_cast<float *>(base + off) = h;
-            *reinterpret_cast<float *>(base + part_bytes + off) = l;
+            base[idx] = __float_as_uint(h);
+            if constexpr (KIND == TC_TF32X3) base[128 * cols_part + idx] = __float_as_uint(tf32_rna((float)(x - (double)h)));
         }
     }
 }
@@ -1014,15 +1080,14 @@ size_t tc_smem_bytes(int katoms)
     using Tr = TcTraits<KIND>;
     constexpr int ECOLS = Tr::NT / 2;
     constexpr int ECH = ECOLS < 16 ? ECOLS : 16;
-    const size_t a = (size_t)katoms * 128 * 128 * Tr::nparts;
     const size_t b = 2 * (size_t)katoms * Tr::NT * 128 * Tr::nparts;
     const size_t kpad = (size_t)katoms * (128 / Tr::esz);
-    return 1024 + a + b + 2 * ECH * 129 * sizeof(float) + 48 * kpad * sizeof(int16_t) + 3 * Tr::NT * sizeof(int2) +
+    return 1024 + b + 2 * ECH * 129 * sizeof(float) + 48 * kpad * sizeof(int16_t) + 3 * Tr::NT * sizeof(int2) +
            16 * sizeof(uint64_t);
 }
 
 template <int KIND, int KATOMS>
-m2l_status launch_atoms(const m2l_ops *ops, const Buckets &b, Layout &L, int a_bytes, const float *in, void *out,
+m2l_status launch_atoms(const m2l_ops *ops, const Buckets &b, Layout &L, const float *in, void *out,
                         int out_fp64, double scale, cudaStream_t s)
 {
     using Tr = TcTraits<KIND>;
@@ -1036,7 +1101,7 @@ m2l_status launch_atoms(const m2l_ops *ops, const Buckets &b, Layout &L, int a_b
     long grid = num_sms();
     const long tiles_bound = (long)(b.nnz + Tr::NT - 1) / Tr::NT + 16;
     if (grid > tiles_bound) grid = tiles_bound;
-    kern<<<(int)grid, kThreadsTC, smem, s>>>(b.rec.as<int2>(), b.class_off.as<int>(), L.a.as<uint8_t>(), a_bytes,
+    kern<<<(int)grid, kThreadsTC, smem, s>>>(b.rec.as<int2>(), b.class_off.as<int>(), L.a.as<uint32_t>(),
                                              L.b.as<int16_t>(), in, out_fp64 ? nullptr : (float *)out,
                                              out_fp64 ? (double *)out : nullptr, ops->n3, (float)scale,
                                              ops->d_status, (ops->debug_flags & M2L_DEBUG_STALL_PRODUCER) ? 1 : 0);
@@ -1060,24 +1125,24 @@ m2l_status launch_kind(const m2l_ops *ops, const Buckets &b, Layout &L, const fl
     }
     if (n3 > 128) return launch_big_ell<KIND>(ops, b, L, in, out, out_fp64, scale, s);
     const int katoms = tc_katoms<KIND>(n3);
-    const int a_bytes = katoms * 128 * 128 * Tr::nparts;
+    const int cols_part = tc_a_cols_part<KIND>(katoms);
+    const size_t a_bytes = (size_t)Tr::nparts * 128 * cols_part * sizeof(uint32_t);
     m2l_status st;
     if (!L.ready) {
         if ((st = L.a.ensure((size_t)16 * a_bytes)) != M2L_OK) return st;
         if ((st = L.b.ensure((size_t)48 * n3 * sizeof(int16_t))) != M2L_OK) return st;
-        M2L_CUDA(cudaMemsetAsync(L.a.p, 0, (size_t)16 * a_bytes, s));
-        dim3 grid((128 * katoms * (128 / Tr::esz) + 255) / 256, 16);
-        a_image_kernel<KIND><<<grid, 256, 0, s>>>(n3, katoms, ops->K64.as<double>(), L.a.as<uint8_t>());
-        M2L_LAUNCH_CHECK("a_image_kernel");
+        dim3 grid((128 * cols_part + 255) / 256, 16);
+        a_tmem_image_kernel<KIND><<<grid, 256, 0, s>>>(n3, cols_part, ops->K64.as<double>(), L.a.as<uint32_t>());
+        M2L_LAUNCH_CHECK("a_tmem_image_kernel");
         sigma_inverse_kernel<<<(48 * n3 + 255) / 256, 256, 0, s>>>(n3, ops->sigma.as<int16_t>(), L.b.as<int16_t>());
         M2L_LAUNCH_CHECK("sigma_inverse_kernel");
         L.ready = true;
     }
     if (b.nnz == 0) return M2L_OK;
-    if (katoms == 1) return launch_atoms<KIND, 1>(ops, b, L, a_bytes, in, out, out_fp64, scale, s);
-    if (katoms == 2) return launch_atoms<KIND, 2>(ops, b, L, a_bytes, in, out, out_fp64, scale, s);
+    if (katoms == 1) return launch_atoms<KIND, 1>(ops, b, L, in, out, out_fp64, scale, s);
+    if (katoms == 2) return launch_atoms<KIND, 2>(ops, b, L, in, out, out_fp64, scale, s);
     if constexpr (KIND != TC_BF16X3)   // bf16 rows hold 64 nodes: ell <= 5 needs at most two columns
-        return launch_atoms<KIND, 4>(ops, b, L, a_bytes, in, out, out_fp64, scale, s);
+        return launch_atoms<KIND, 4>(ops, b, L, in, out, out_fp64, scale, s);
     set_error("no tensor-core configuration for %d swizzle columns", katoms);
     return M2L_EUNSUPPORTED;
 }
