@@ -3,7 +3,9 @@
 // One persistent CTA per SM walks a contiguous range of tiles; a tile is NT
 // bucketed interactions of one unique operator K_p (Alg. 2, blocked along many
 // target cells as in Sec. 4.2.3).  Warp roles:
-//   warps 0-7  producers: per tile, gather the NT source multipoles and
+//   warps 0-7  producers: per tile, gather the NT source multipoles (one
+//              column per warp at a time, lane l taking K elements
+//              [EPL l, EPL (l+1)), so a warp-wide load reads one vector) and
 //              permute them (W_p[sigma_g(b)][c] = w[b], Eq. (30)) straight into
 //              a 128-byte-swizzled K-major shared-memory panel (the UMMA B
 //              operand), rounded to TF32 or split into BF16/TF32 hi + lo;
@@ -258,6 +260,15 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
 
 __host__ __device__ constexpr int tmem_alloc_cols(int n) { return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : n <= 256 ? 256 : 512; }
 
+// NW consecutive 32-bit words to shared memory in one store (address aligned to 4 NW bytes).
+template <int NW>
+__device__ __forceinline__ void st_shared_words(uint8_t *p, const uint32_t (&w)[NW])
+{
+    if constexpr (NW == 4) *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    else if constexpr (NW == 2) *reinterpret_cast<uint2 *>(p) = make_uint2(w[0], w[1]);
+    else *reinterpret_cast<uint32_t *>(p) = w[0];
+}
+
 __device__ __forceinline__ float tf32_rna(float x)
 {
     uint32_t r;
@@ -306,18 +317,17 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
     constexpr int ELEMS_PER_ATOM = 128 / Tr::esz;           // K elements per 128-byte row
     constexpr int K_PER_MMA = 32 / Tr::esz;                  // 8 (tf32) or 16 (bf16)
     constexpr int MMAS_PER_ATOM = ELEMS_PER_ATOM / K_PER_MMA;  // 4
-    constexpr int EPC = 16 / Tr::esz;                        // elements per 16-byte chunk
     constexpr int KPAD = KATOMS * ELEMS_PER_ATOM;            // padded K (source nodes)
-    constexpr int CPC = KATOMS * 8;                          // 16-byte chunks per column and part
     constexpr int NPT = kProducerWarps * 32;                 // producer threads
-    constexpr int NCG = NPT / CPC;                           // column stride of a producer thread
-    constexpr int CPT = (NT + NCG - 1) / NCG;                // columns per producer thread
+    constexpr int EPL = KPAD / 32;                           // K elements per lane and column
+    constexpr int CPW = NT / kProducerWarps;                 // columns per producer warp
+    constexpr int NWL = EPL * Tr::esz / 4;                   // 32-bit words per lane, column and part
     constexpr int A_COLS_PART = tc_a_cols_part<KIND>(KATOMS);  // TMEM columns of one part of A
     constexpr int B_PART = KATOMS * NT * 128;                // one operand part of a B stage
     constexpr int B_STAGE = B_PART * Tr::nparts;
     constexpr int ECOLS = NT / 2;                            // columns per epilogue group and tile
     constexpr int ECH = ECOLS < 16 ? ECOLS : 16;             // columns per TMEM load
-    static_assert(NPT % CPC == 0, "producer mapping");
+    static_assert(KPAD % 32 == 0 && NT % kProducerWarps == 0 && NWL >= 1, "producer mapping");
     static_assert(ECOLS % ECH == 0 && (ECH == 16 || ECH == 8), "epilogue chunking");
 
     extern __shared__ uint8_t smem_raw[];
@@ -389,9 +399,12 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
 
     if (warp < kProducerWarps) {
         // ------------------------------------------------------------ producers
+        // warp w fills columns w, w + 8, ...; lane l the K elements [EPL l, EPL (l + 1)) of
+        // each, so that one warp-wide gather reads a single source vector
         const int ptid = threadIdx.x;
-        const int j = ptid % CPC;            // 16-byte chunk of the column this thread fills
-        const int cg = ptid / CPC;           // first column of this thread
+        const int kbyte = EPL * lane * Tr::esz;                       // byte position along K
+        const uint32_t lane_off = (uint32_t)(kbyte >> 7) * (uint32_t)(NT * 128);  // swizzle column
+        const int lane_chunk = (kbyte & 127) >> 4, lane_within = kbyte & 15;
         int prev_p = -1;
         // records are fetched one tile ahead, into a register of thread c < NT
         int2 nxt = make_int2(0, 0);
@@ -450,43 +463,39 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
             }
             named_bar_sync(2, NPT);
             // issue every gather of this thread before waiting for the stage
-            float v[CPT][EPC];
+            float v[CPW][EPL];
 #pragma unroll
-            for (int u = 0; u < CPT; ++u) {
-                const int c = cg + u * NCG;
+            for (int u = 0; u < CPW; ++u) {
+                const int c = warp + u * kProducerWarps;
                 const bool live = (c < nc);
                 const int2 r = live ? prec[c] : make_int2(0, 0);
                 const float *w = mp + (size_t)r.x * n3;
-                const int16_t *si = s_sinv + rec_g(r.y) * KPAD + EPC * j;
-                int16_t idx[EPC];
-                if constexpr (EPC == 4) {
+                const int16_t *si = s_sinv + rec_g(r.y) * KPAD + EPL * lane;
+                int idx[EPL];
+                if constexpr (EPL == 4) {
                     const uint2 q = *reinterpret_cast<const uint2 *>(si);
                     idx[0] = (int16_t)(q.x & 0xFFFF); idx[1] = (int16_t)(q.x >> 16);
                     idx[2] = (int16_t)(q.y & 0xFFFF); idx[3] = (int16_t)(q.y >> 16);
+                } else if constexpr (EPL == 2) {
+                    const uint32_t q = *reinterpret_cast<const uint32_t *>(si);
+                    idx[0] = (int16_t)(q & 0xFFFF); idx[1] = (int16_t)(q >> 16);
                 } else {
-                    const uint4 q = *reinterpret_cast<const uint4 *>(si);
-                    const uint32_t qq[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        idx[2 * e] = (int16_t)(qq[e] & 0xFFFF);
-                        idx[2 * e + 1] = (int16_t)(qq[e] >> 16);
-                    }
+                    idx[0] = si[0];
                 }
 #pragma unroll
-                for (int e = 0; e < EPC; ++e) v[u][e] = live ? __ldg(w + idx[e]) : 0.0f;
+                for (int e = 0; e < EPL; ++e) v[u][e] = live ? __ldg(w + idx[e]) : 0.0f;
             }
             const bool ok = mbar_wait(empty + s, (k & 1) ^ 1, abort_flag, status);
             if (named_bar_or(2, NPT, ok ? 0 : 1)) break;
             uint8_t *stage = sB + s * B_STAGE;
 #pragma unroll
-            for (int u = 0; u < CPT; ++u) {
-                const int c = cg + u * NCG;
-                if (c >= NT) break;
-                const uint32_t off = (uint32_t)(j >> 3) * (uint32_t)(NT * 128) + swz_off(c, j & 7);
+            for (int u = 0; u < CPW; ++u) {
+                const int c = warp + u * kProducerWarps;
+                uint8_t *dst = stage + lane_off + swz_off(c, lane_chunk) + lane_within;
+                uint32_t hi[NWL], lo[NWL];
                 if constexpr (KIND == TC_BF16X3) {
-                    uint32_t hi[4], lo[4];
 #pragma unroll
-                    for (int e = 0; e < 8; e += 2) {
+                    for (int e = 0; e < EPL; e += 2) {
                         const __nv_bfloat16 h0 = __float2bfloat16_rn(v[u][e]);
                         const __nv_bfloat16 h1 = __float2bfloat16_rn(v[u][e + 1]);
                         const __nv_bfloat16 l0 = __float2bfloat16_rn(v[u][e] - __bfloat162float(h0));
@@ -494,21 +503,16 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
                         hi[e / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
                         lo[e / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
                     }
-                    *reinterpret_cast<uint4 *>(stage + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                    *reinterpret_cast<uint4 *>(stage + B_PART + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-                } else if constexpr (KIND == TC_TF32) {
-                    *reinterpret_cast<float4 *>(stage + off) =
-                        make_float4(tf32_rna(v[u][0]), tf32_rna(v[u][1]), tf32_rna(v[u][2]), tf32_rna(v[u][3]));
                 } else {
-                    float h[4], l[4];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        h[e] = tf32_rna(v[u][e]);
-                        l[e] = tf32_rna(v[u][e] - h[e]);
+                    for (int e = 0; e < EPL; ++e) {
+                        const float h = tf32_rna(v[u][e]);
+                        hi[e] = __float_as_uint(h);
+                        lo[e] = __float_as_uint(tf32_rna(v[u][e] - h));
                     }
-                    *reinterpret_cast<float4 *>(stage + off) = make_float4(h[0], h[1], h[2], h[3]);
-                    *reinterpret_cast<float4 *>(stage + B_PART + off) = make_float4(l[0], l[1], l[2], l[3]);
                 }
+                st_shared_words<NWL>(dst, hi);
+                if constexpr (Tr::nparts == 2) st_shared_words<NWL>(dst + B_PART, lo);
             }
             fence_proxy_async();
             // stall_first_stage (a test switch) withholds the first stage's signal, so the
