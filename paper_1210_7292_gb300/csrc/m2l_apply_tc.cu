@@ -288,11 +288,12 @@ struct TileSched {
     int first, last;   // [first, last) tile indices of this CTA
 };
 
-// Tile t -> (operator p, first bucketed column, column count).
+// Tile t -> (operator p, first bucketed column, column count).  p is a cursor:
+// it starts at 0 and each caller asks for non-decreasing t, so the search
+// moves only at operator boundaries.
 __device__ __forceinline__ void tile_info(int t, const int *tile_start, const int *class_off, int NT, int &p,
                                           int &col0, int &nc)
 {
-    p = 0;
     while (p < 15 && t >= tile_start[p + 1]) ++p;
     col0 = class_off[p] + (t - tile_start[p]) * NT;
     nc = min(NT, class_off[p + 1] - col0);
@@ -406,16 +407,17 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
         const uint32_t lane_off = (uint32_t)(kbyte >> 7) * (uint32_t)(NT * 128);  // swizzle column
         const int lane_chunk = (kbyte & 127) >> 4, lane_within = kbyte & 15;
         int prev_p = -1;
+        int p = 0, p1 = 0;                   // operator cursors of this tile and of the next
         // records are fetched one tile ahead, into a register of thread c < NT
         int2 nxt = make_int2(0, 0);
         if (first < last && ptid < NT) {
-            int p0, c00, nc0;
-            tile_info(first, s_tile_start, class_off, NT, p0, c00, nc0);
+            int c00, nc0;
+            tile_info(first, s_tile_start, class_off, NT, p1, c00, nc0);
             if (ptid < nc0) nxt = __ldg(rec + c00 + ptid);
         }
         for (int t = first; t < last; ++t) {
             const int i = t - first, s = i & 1, k = i >> 1;
-            int p, col0, nc;
+            int col0, nc;
             tile_info(t, s_tile_start, class_off, NT, p, col0, nc);
             if (p != prev_p) {
                 // the operator changes: once the MMAs of the previous tile (the last readers
@@ -456,7 +458,7 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
                 prec[ptid] = nxt;
                 nxt = make_int2(0, 0);
                 if (t + 1 < last) {
-                    int p1, c01, nc1;
+                    int c01, nc1;
                     tile_info(t + 1, s_tile_start, class_off, NT, p1, c01, nc1);
                     if (ptid < nc1) nxt = __ldg(rec + c01 + ptid);
                 }
@@ -496,12 +498,13 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
                 if constexpr (KIND == TC_BF16X3) {
 #pragma unroll
                     for (int e = 0; e < EPL; e += 2) {
-                        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[u][e]);
-                        const __nv_bfloat16 h1 = __float2bfloat16_rn(v[u][e + 1]);
-                        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[u][e] - __bfloat162float(h0));
-                        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[u][e + 1] - __bfloat162float(h1));
-                        hi[e / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                        lo[e / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                        // two values per conversion, the even K index in the low half
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[u][e], v[u][e + 1]);
+                        const uint32_t hu = *reinterpret_cast<const uint32_t *>(&h2);
+                        const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[u][e] - __uint_as_float(hu << 16),
+                                                                        v[u][e + 1] - __uint_as_float(hu & 0xFFFF0000u));
+                        hi[e / 2] = hu;
+                        lo[e / 2] = *reinterpret_cast<const uint32_t *>(&l2);
                     }
                 } else {
 #pragma unroll
@@ -524,12 +527,12 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
         if (lane == 0) {
             const uint32_t idesc = instr_desc(Tr::fmt, NT);
             const uint32_t a_base = tmem_base + (uint32_t)A_COL0, b_base = smem_u32(sB);
-            int prev_p = -1;
+            int prev_p = -1, p = 0;
             uint32_t a_loads = 0;
             bool issued = false;
             for (int t = first; t < last; ++t) {
                 const int i = t - first, s = i & 1, k = i >> 1;
-                int p, col0, nc;
+                int col0, nc;
                 tile_info(t, s_tile_start, class_off, NT, p, col0, nc);
                 if (!mbar_wait(full + s, k & 1, abort_flag, status)) break;
                 if (p != prev_p) {
@@ -588,22 +591,20 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
         const int gc0 = G * ECOLS;                        // first tile column of this group
         // records are fetched one tile ahead, into a register of thread a < ECOLS (y = -1: dead column)
         int nxt = -1;
+        int p1 = 0;                                       // operator cursor of the next tile
         if (first < last && a < ECOLS) {
-            int p0, c00, nc0;
-            tile_info(first, s_tile_start, class_off, NT, p0, c00, nc0);
+            int c00, nc0;
+            tile_info(first, s_tile_start, class_off, NT, p1, c00, nc0);
             if (a < nc0 - gc0) nxt = __ldg(rec + c00 + gc0 + a).y;
         }
         for (int t = first; t < last; ++t) {
             const int i = t - first, ab = i % NACC, ak = i / NACC;
-            int p, col0, nc;
-            tile_info(t, s_tile_start, class_off, NT, p, col0, nc);
-            const int gnc = min(ECOLS, nc - gc0);         // live columns of this group (may be <= 0)
             if (a < ECOLS) {
                 e_goff[a] = (nxt == -1 ? 0 : rec_g(nxt)) * KPAD;
                 e_tgt[a] = (nxt == -1) ? -1 : rec_tgt(nxt);
                 nxt = -1;
                 if (t + 1 < last) {
-                    int p1, c01, nc1;
+                    int c01, nc1;
                     tile_info(t + 1, s_tile_start, class_off, NT, p1, c01, nc1);
                     if (a < nc1 - gc0) nxt = __ldg(rec + c01 + gc0 + a).y;
                 }
@@ -632,37 +633,31 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
                     for (int jj = 0; jj < ECH; ++jj) sFg[jj * 129 + s_sinv[go[jj] + row]] = v[jj];
                 }
                 named_bar_sync(bar_id, 128);
-                if (a < n3) {
-                    float x[ECH];
-                    int tg[ECH];
+                // run starts of this chunk as one warp ballot: lane jj tests column jj, live and
+                // with a target other than its predecessor's (the dead columns of a ragged tile
+                // come last, so the predecessor of a live column is live or the open run)
+                unsigned bm;
+                {
+                    const int jl = lane < ECH ? lane : ECH - 1;
+                    const int tj = e_tgt[ECH * ch + jl];
+                    const int tp = (jl > 0) ? e_tgt[ECH * ch + jl - 1] : (ch > 0 ? e_tgt[ECH * ch - 1] : cur);
+                    bm = __ballot_sync(0xffffffffu, lane < ECH && tj >= 0 && tj != tp);
+                }
+                // rows a >= n3 of the transpose are never written: read (in bounds) and never added
+                float x[ECH];
 #pragma unroll
-                    for (int jj = 0; jj < ECH; ++jj) x[jj] = sFg[jj * 129 + a];
+                for (int jj = 0; jj < ECH; ++jj) x[jj] = sFg[jj * 129 + a];
 #pragma unroll
-                    for (int v4 = 0; v4 < ECH / 4; ++v4) {
-                        const int4 y = *reinterpret_cast<const int4 *>(e_tgt + ECH * ch + 4 * v4);
-                        tg[4 * v4] = y.x; tg[4 * v4 + 1] = y.y; tg[4 * v4 + 2] = y.z; tg[4 * v4 + 3] = y.w;
-                    }
-                    // columns where a new target run starts, found without branches (a dead
-                    // column of a ragged tile holds zeros and starts no run)
-                    unsigned bm = 0u;
-                    int prev = cur;
-#pragma unroll
-                    for (int jj = 0; jj < ECH; ++jj) {
-                        bm |= ((tg[jj] >= 0 && tg[jj] != prev) ? 1u : 0u) << jj;
-                        prev = tg[jj] >= 0 ? tg[jj] : prev;
-                    }
-#pragma unroll
-                    for (int jj = 0; jj < ECH; ++jj) {
-                        if (bm & (1u << jj)) {
-                            if (cur >= 0) {
-                                if (out_f64) atomicAdd(out_f64 + (size_t)cur * n3 + a, (double)acc * (double)scale);
-                                else atomicAdd(out_f32 + (size_t)cur * n3 + a, acc * scale);
-                            }
-                            acc = 0.0f;
-                            cur = tg[jj];
+                for (int jj = 0; jj < ECH; ++jj) {
+                    if (bm & (1u << jj)) {
+                        if (cur >= 0 && a < n3) {
+                            if (out_f64) atomicAdd(out_f64 + (size_t)cur * n3 + a, (double)acc * (double)scale);
+                            else atomicAdd(out_f32 + (size_t)cur * n3 + a, acc * scale);
                         }
-                        acc += x[jj];
+                        acc = 0.0f;
+                        cur = e_tgt[ECH * ch + jj];
                     }
+                    acc += x[jj];
                 }
                 named_bar_sync(bar_id, 128);
             }
@@ -785,9 +780,10 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
     if (warp < kProducerWarps) {
         // ------------------------------------------------------------ panel producers
         const int ptid = threadIdx.x;
+        int p = 0;   // operator cursor (tile_info)
         for (int t = first; t < last; ++t) {
             const int i = t - first, s = i % NB, ks = i / NB;
-            int p, col0, nc;
+            int col0, nc;
             tile_info(t, s_tile_start, class_off, NT, p, col0, nc);
             int2 *prec = s_prec + s * NT;
             if (ptid < NT) prec[ptid] = (ptid < nc) ? __ldg(rec + col0 + ptid) : make_int2(0, 0);
@@ -912,9 +908,10 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
         // ------------------------------------------------------------ operator blocks
         if (lane == 0) {
             int last_u[4] = {-1, -1, -1, -1};
+            int p = 0;   // operator cursor (tile_info)
             for (int t = first; t < last; ++t) {
                 const int i = t - first;
-                int p, col0, nc;
+                int col0, nc;
                 tile_info(t, s_tile_start, class_off, NT, p, col0, nc);
                 bool ok = true;
                 for (int mt = 0; mt < MT && ok; ++mt)
@@ -942,9 +939,10 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
         float acc[MT];
 #pragma unroll
         for (int k = 0; k < MT; ++k) acc[k] = 0.0f;
+        int p = 0;   // operator cursor (tile_info)
         for (int t = first; t < last; ++t) {
             const int i = t - first, buf = i & 1, kb = i >> 1;
-            int p, col0, nc;
+            int col0, nc;
             tile_info(t, s_tile_start, class_off, NT, p, col0, nc);
             if (a < NT) {
                 const int2 r = (a < nc) ? __ldg(rec + col0 + a) : make_int2(0, 0);
