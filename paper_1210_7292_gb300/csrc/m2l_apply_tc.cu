@@ -310,8 +310,8 @@ template <int KIND, int KATOMS>
 __global__ void __launch_bounds__(kThreadsTC, 1)
 tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
                 const uint32_t *__restrict__ a_img, const int16_t *__restrict__ sigma_inv,
-                const float *__restrict__ mp, float *__restrict__ out_f32, double *__restrict__ out_f64, int n3,
-                float scale, int *status, int stall_first_stage)
+                const float *__restrict__ mp, float *__restrict__ out_f32, double *__restrict__ out_f64, int ell,
+                int n3, float scale, int *status, int stall_first_stage)
 {
     using Tr = TcTraits<KIND>;
     constexpr int NT = Tr::NT;
@@ -340,8 +340,9 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
     float *sF = reinterpret_cast<float *>(sB + 2 * B_STAGE);          // [2 groups][ECH][129] transposes
     int16_t *s_sinv = reinterpret_cast<int16_t *>(sF + 2 * ECH * 129);  // [48][KPAD] inverse permutations
     int2 *s_prec = reinterpret_cast<int2 *>(s_sinv + 48 * KPAD);      // [2][NT] producer records
-    int2 *s_erec = s_prec + 2 * NT;                                   // [2 groups][2][ECOLS] ints: column tables
-    uint64_t *bars = reinterpret_cast<uint64_t *>(s_erec + NT);
+    int2 *s_erec = s_prec + 2 * NT;                                   // [NT] writer + [NT] int target tables
+    int2 *s_gaff = s_erec + 2 * NT;                                   // [48] affine form of sigma_g^{-1}
+    uint64_t *bars = reinterpret_cast<uint64_t *>(s_gaff + 48);
     uint64_t *full = bars, *empty = bars + 2, *tfull = bars + 4, *tempty = bars + 8, *a_ready = bars + 12,
              *drain = bars + 13;
     __shared__ uint32_t s_tmem_base;
@@ -361,6 +362,18 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
     for (int idx = threadIdx.x; idx < 48 * KPAD; idx += blockDim.x) {
         const int g = idx / KPAD, kk = idx % KPAD;
         s_sinv[idx] = (kk < n3) ? sigma_inv[g * n3 + kk] : (int16_t)0;
+    }
+    // sigma_g^{-1} is a signed axis permutation of the node digits, hence affine in
+    // them: sigma_g^{-1}(a') = C + sum_e M_e d_e(a'), with C = sigma_g^{-1}(0) and
+    // M_e = sigma_g^{-1}(ell^e) - C.  Kept as the byte multipliers 4 M_e (a dp4a
+    // operand, |4 M_e| <= 4 ell^2 <= 100 for ell <= 5) and 4 C.
+    if (threadIdx.x < 48) {
+        const int g = threadIdx.x;
+        const int c0 = sigma_inv[g * n3];
+        uint32_t m = 0;
+        for (int e = 0, pw = 1; e < 3; ++e, pw *= ell)
+            m |= ((uint32_t)(4 * (sigma_inv[g * n3 + pw] - c0)) & 0xFFu) << (8 * e);
+        s_gaff[g] = make_int2((int)m, 4 * c0);
     }
     if (threadIdx.x == 0) {
         int acc = 0;
@@ -584,8 +597,13 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
         const int row = 32 * q + lane;                 // accumulator row (permuted node a')
         const int bar_id = 1 + 2 * G;                  // named barriers 1 and 3
         float *sFg = sF + G * ECH * 129;
-        int *e_goff = reinterpret_cast<int *>(s_erec) + G * 2 * ECOLS;   // [ECOLS] g * KPAD per column
-        int *e_tgt = e_goff + ECOLS;                                      // [ECOLS] target, -1 when dead
+        // per column of this group: the dp4a multipliers of its sigma and the byte address of
+        // node 0 of its transpose column; and its target (-1: dead column)
+        int2 *e_wt = s_erec + G * ECOLS;
+        int *e_tgt = reinterpret_cast<int *>(s_erec + NT) + G * ECOLS;
+        // digits of a' in signed bytes, the other dp4a operand
+        const int xd = (row % ell) | ((row / ell % ell) << 8) | ((row / (ell * ell)) << 16);
+        const int col_addr = (int)smem_u32(sFg) + (a % ECH) * 129 * 4;   // used by threads a < ECOLS
         int cur = -1;
         float acc = 0.0f;
         const int gc0 = G * ECOLS;                        // first tile column of this group
@@ -600,7 +618,8 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
         for (int t = first; t < last; ++t) {
             const int i = t - first, ab = i % NACC, ak = i / NACC;
             if (a < ECOLS) {
-                e_goff[a] = (nxt == -1 ? 0 : rec_g(nxt)) * KPAD;
+                const int2 ga = s_gaff[nxt == -1 ? 0 : rec_g(nxt)];
+                e_wt[a] = make_int2(ga.x, ga.y + col_addr);
                 e_tgt[a] = (nxt == -1) ? -1 : rec_tgt(nxt);
                 nxt = -1;
                 if (t + 1 < last) {
@@ -623,14 +642,13 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
                 }
                 // un-permute on the write: row a' of column jj lands at node sigma_g^{-1}(a')
                 if (row < n3) {
-                    int go[ECH];
+                    const int2 *wt = e_wt + ECH * ch;
 #pragma unroll
-                    for (int v4 = 0; v4 < ECH / 4; ++v4) {
-                        const int4 x = *reinterpret_cast<const int4 *>(e_goff + ECH * ch + 4 * v4);
-                        go[4 * v4] = x.x; go[4 * v4 + 1] = x.y; go[4 * v4 + 2] = x.z; go[4 * v4 + 3] = x.w;
+                    for (int jj = 0; jj < ECH; ++jj) {
+                        const int2 e = wt[jj];
+                        const uint32_t addr = (uint32_t)__dp4a(xd, e.x, e.y);
+                        asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(v[jj]) : "memory");
                     }
-#pragma unroll
-                    for (int jj = 0; jj < ECH; ++jj) sFg[jj * 129 + s_sinv[go[jj] + row]] = v[jj];
                 }
                 named_bar_sync(bar_id, 128);
                 // run starts of this chunk as one warp ballot: lane jj tests column jj, live and
@@ -648,16 +666,24 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
 #pragma unroll
                 for (int jj = 0; jj < ECH; ++jj) x[jj] = sFg[jj * 129 + a];
 #pragma unroll
-                for (int jj = 0; jj < ECH; ++jj) {
-                    if (bm & (1u << jj)) {
-                        if (cur >= 0 && a < n3) {
-                            if (out_f64) atomicAdd(out_f64 + (size_t)cur * n3 + a, (double)acc * (double)scale);
-                            else atomicAdd(out_f32 + (size_t)cur * n3 + a, acc * scale);
-                        }
-                        acc = 0.0f;
-                        cur = e_tgt[ECH * ch + jj];
+                for (int h = 0; h < ECH; h += 8) {
+                    if (((bm >> h) & 0xFFu) == 0u) {
+                        // no run starts in these eight columns: one tree sum
+                        acc += ((x[h] + x[h + 1]) + (x[h + 2] + x[h + 3])) + ((x[h + 4] + x[h + 5]) + (x[h + 6] + x[h + 7]));
+                        continue;
                     }
-                    acc += x[jj];
+#pragma unroll
+                    for (int jj = h; jj < h + 8; ++jj) {
+                        if (bm & (1u << jj)) {
+                            if (cur >= 0 && a < n3) {
+                                if (out_f64) atomicAdd(out_f64 + (size_t)cur * n3 + a, (double)acc * (double)scale);
+                                else atomicAdd(out_f32 + (size_t)cur * n3 + a, acc * scale);
+                            }
+                            acc = 0.0f;
+                            cur = e_tgt[ECH * ch + jj];
+                        }
+                        acc += x[jj];
+                    }
                 }
                 named_bar_sync(bar_id, 128);
             }
@@ -1084,8 +1110,8 @@ size_t tc_smem_bytes(int katoms)
     constexpr int ECH = ECOLS < 16 ? ECOLS : 16;
     const size_t b = 2 * (size_t)katoms * Tr::NT * 128 * Tr::nparts;
     const size_t kpad = (size_t)katoms * (128 / Tr::esz);
-    return 1024 + b + 2 * ECH * 129 * sizeof(float) + 48 * kpad * sizeof(int16_t) + 3 * Tr::NT * sizeof(int2) +
-           16 * sizeof(uint64_t);
+    return 1024 + b + 2 * ECH * 129 * sizeof(float) + 48 * kpad * sizeof(int16_t) +
+           (4 * Tr::NT + 48) * sizeof(int2) + 16 * sizeof(uint64_t);
 }
 
 template <int KIND, int KATOMS>
@@ -1105,7 +1131,7 @@ m2l_status launch_atoms(const m2l_ops *ops, const Buckets &b, Layout &L, const f
     if (grid > tiles_bound) grid = tiles_bound;
     kern<<<(int)grid, kThreadsTC, smem, s>>>(b.rec.as<int2>(), b.class_off.as<int>(), L.a.as<uint32_t>(),
                                              L.b.as<int16_t>(), in, out_fp64 ? nullptr : (float *)out,
-                                             out_fp64 ? (double *)out : nullptr, ops->n3, (float)scale,
+                                             out_fp64 ? (double *)out : nullptr, ops->ell, ops->n3, (float)scale,
                                              ops->d_status, (ops->debug_flags & M2L_DEBUG_STALL_PRODUCER) ? 1 : 0);
     M2L_LAUNCH_CHECK("tc_apply_kernel");
     return M2L_OK;
