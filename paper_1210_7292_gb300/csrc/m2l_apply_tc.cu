@@ -16,7 +16,8 @@
 //              F_p = K_p W_p (Eq. (31)) into one of three or four TMEM
 //              accumulators, three products hi*hi + hi*lo + lo*hi for the
 //              split precisions.
-//   warps 9-16 epilogue (two groups of four, each owning half the columns): tcgen05.ld of the accumulator, un-permutation
+//   warps 9-24 epilogue (four groups of four, each owning a quarter of the
+//              columns of every tile): tcgen05.ld of the accumulator, un-permutation
 //              f[a] += F_p[sigma_g(a)] (Eq. (32)) through a shared-memory
 //              transpose, sum over the consecutive columns of one target,
 //              one atomic add per (target, node) and run (Alg. 2, third loop).
@@ -33,7 +34,8 @@ namespace {
 constexpr int kProducerWarps = 8;
 constexpr int kMmaWarp = 8;
 constexpr int kEpiWarp0 = 9;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiGroups = 4;                        // epilogue groups of four warps
+constexpr int kEpiWarps = 4 * kEpiGroups;
 constexpr int kThreadsTC = (kProducerWarps + 1 + kEpiWarps) * 32;
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 constexpr uint32_t kSuspendHintNs = 20000;         // longest park of one try_wait
@@ -322,11 +324,13 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
     constexpr int NPT = kProducerWarps * 32;                 // producer threads
     constexpr int EPL = KPAD / 32;                           // K elements per lane and column
     constexpr int CPW = NT / kProducerWarps;                 // columns per producer warp
+    constexpr int NPASS = CPW >= 16 ? 2 : 1;                 // gather passes per tile (register budget)
+    constexpr int CPP = CPW / NPASS;                         // columns per warp and pass
     constexpr int NWL = EPL * Tr::esz / 4;                   // 32-bit words per lane, column and part
     constexpr int A_COLS_PART = tc_a_cols_part<KIND>(KATOMS);  // TMEM columns of one part of A
     constexpr int B_PART = KATOMS * NT * 128;                // one operand part of a B stage
     constexpr int B_STAGE = B_PART * Tr::nparts;
-    constexpr int ECOLS = NT / 2;                            // columns per epilogue group and tile
+    constexpr int ECOLS = NT / kEpiGroups;                   // columns per epilogue group and tile
     constexpr int ECH = ECOLS < 16 ? ECOLS : 16;             // columns per TMEM load
     static_assert(KPAD % 32 == 0 && NT % kProducerWarps == 0 && NWL >= 1, "producer mapping");
     static_assert(ECOLS % ECH == 0 && (ECH == 16 || ECH == 8), "epilogue chunking");
@@ -337,11 +341,11 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
     // turn them into generic ones)
     uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint8_t *sB = smem;                                               // 2 stages
-    float *sF = reinterpret_cast<float *>(sB + 2 * B_STAGE);          // [2 groups][ECH][129] transposes
-    int16_t *s_sinv = reinterpret_cast<int16_t *>(sF + 2 * ECH * 129);  // [48][KPAD] inverse permutations
+    float *sF = reinterpret_cast<float *>(sB + 2 * B_STAGE);          // [groups][2 buffers][ECH][129]
+    int16_t *s_sinv = reinterpret_cast<int16_t *>(sF + 2 * kEpiGroups * ECH * 129);  // [48][KPAD] inverse perms
     int2 *s_prec = reinterpret_cast<int2 *>(s_sinv + 48 * KPAD);      // [2][NT] producer records
-    int2 *s_erec = s_prec + 2 * NT;                                   // [NT] writer + [NT] int target tables
-    int2 *s_gaff = s_erec + 2 * NT;                                   // [48] affine form of sigma_g^{-1}
+    int2 *s_erec = s_prec + 2 * NT;                                   // [2][NT] writer + [2][NT] int target tables
+    int2 *s_gaff = s_erec + 3 * NT;                                   // [48] affine form of sigma_g^{-1}
     uint64_t *bars = reinterpret_cast<uint64_t *>(s_gaff + 48);
     uint64_t *full = bars, *empty = bars + 2, *tfull = bars + 4, *tempty = bars + 8, *a_ready = bars + 12,
              *drain = bars + 13;
@@ -477,59 +481,70 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
                 }
             }
             named_bar_sync(2, NPT);
-            // issue every gather of this thread before waiting for the stage
-            float v[CPW][EPL];
-#pragma unroll
-            for (int u = 0; u < CPW; ++u) {
-                const int c = warp + u * kProducerWarps;
-                const bool live = (c < nc);
-                const int2 r = live ? prec[c] : make_int2(0, 0);
-                const float *w = mp + (size_t)r.x * n3;
-                const int16_t *si = s_sinv + rec_g(r.y) * KPAD + EPL * lane;
-                int idx[EPL];
-                if constexpr (EPL == 4) {
-                    const uint2 q = *reinterpret_cast<const uint2 *>(si);
-                    idx[0] = (int16_t)(q.x & 0xFFFF); idx[1] = (int16_t)(q.x >> 16);
-                    idx[2] = (int16_t)(q.y & 0xFFFF); idx[3] = (int16_t)(q.y >> 16);
-                } else if constexpr (EPL == 2) {
-                    const uint32_t q = *reinterpret_cast<const uint32_t *>(si);
-                    idx[0] = (int16_t)(q & 0xFFFF); idx[1] = (int16_t)(q >> 16);
-                } else {
-                    idx[0] = si[0];
-                }
-#pragma unroll
-                for (int e = 0; e < EPL; ++e) v[u][e] = live ? __ldg(w + idx[e]) : 0.0f;
-            }
-            const bool ok = mbar_wait(empty + s, (k & 1) ^ 1, abort_flag, status);
-            if (named_bar_or(2, NPT, ok ? 0 : 1)) break;
             uint8_t *stage = sB + s * B_STAGE;
+            bool stop = false;
 #pragma unroll
-            for (int u = 0; u < CPW; ++u) {
-                const int c = warp + u * kProducerWarps;
-                uint8_t *dst = stage + lane_off + swz_off(c, lane_chunk) + lane_within;
-                uint32_t hi[NWL], lo[NWL];
-                if constexpr (KIND == TC_BF16X3) {
+            for (int pass = 0; pass < NPASS; ++pass) {
+                // issue every gather of this pass before the stores (the first pass also
+                // before waiting for the stage)
+                float v[CPP][EPL];
 #pragma unroll
-                    for (int e = 0; e < EPL; e += 2) {
-                        // two values per conversion, the even K index in the low half
-                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[u][e], v[u][e + 1]);
-                        const uint32_t hu = *reinterpret_cast<const uint32_t *>(&h2);
-                        const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[u][e] - __uint_as_float(hu << 16),
-                                                                        v[u][e + 1] - __uint_as_float(hu & 0xFFFF0000u));
-                        hi[e / 2] = hu;
-                        lo[e / 2] = *reinterpret_cast<const uint32_t *>(&l2);
+                for (int uu = 0; uu < CPP; ++uu) {
+                    const int c = warp + (pass * CPP + uu) * kProducerWarps;
+                    const bool live = (c < nc);
+                    const int2 r = live ? prec[c] : make_int2(0, 0);
+                    const float *w = mp + (size_t)r.x * n3;
+                    const int16_t *si = s_sinv + rec_g(r.y) * KPAD + EPL * lane;
+                    int idx[EPL];
+                    if constexpr (EPL == 4) {
+                        const uint2 q = *reinterpret_cast<const uint2 *>(si);
+                        idx[0] = (int16_t)(q.x & 0xFFFF); idx[1] = (int16_t)(q.x >> 16);
+                        idx[2] = (int16_t)(q.y & 0xFFFF); idx[3] = (int16_t)(q.y >> 16);
+                    } else if constexpr (EPL == 2) {
+                        const uint32_t q = *reinterpret_cast<const uint32_t *>(si);
+                        idx[0] = (int16_t)(q & 0xFFFF); idx[1] = (int16_t)(q >> 16);
+                    } else {
+                        idx[0] = si[0];
                     }
-                } else {
 #pragma unroll
-                    for (int e = 0; e < EPL; ++e) {
-                        const float h = tf32_rna(v[u][e]);
-                        hi[e] = __float_as_uint(h);
-                        lo[e] = __float_as_uint(tf32_rna(v[u][e] - h));
+                    for (int e = 0; e < EPL; ++e) v[uu][e] = live ? __ldg(w + idx[e]) : 0.0f;
+                }
+                if (pass == 0) {
+                    const bool ok = mbar_wait(empty + s, (k & 1) ^ 1, abort_flag, status);
+                    if (named_bar_or(2, NPT, ok ? 0 : 1)) {
+                        stop = true;
+                        break;
                     }
                 }
-                st_shared_words<NWL>(dst, hi);
-                if constexpr (Tr::nparts == 2) st_shared_words<NWL>(dst + B_PART, lo);
+#pragma unroll
+                for (int uu = 0; uu < CPP; ++uu) {
+                    const int c = warp + (pass * CPP + uu) * kProducerWarps;
+                    uint8_t *dst = stage + lane_off + swz_off(c, lane_chunk) + lane_within;
+                    uint32_t hi[NWL], lo[NWL];
+                    if constexpr (KIND == TC_BF16X3) {
+#pragma unroll
+                        for (int e = 0; e < EPL; e += 2) {
+                            // two values per conversion, the even K index in the low half
+                            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[uu][e], v[uu][e + 1]);
+                            const uint32_t hu = *reinterpret_cast<const uint32_t *>(&h2);
+                            const __nv_bfloat162 l2 = __floats2bfloat162_rn(
+                                v[uu][e] - __uint_as_float(hu << 16), v[uu][e + 1] - __uint_as_float(hu & 0xFFFF0000u));
+                            hi[e / 2] = hu;
+                            lo[e / 2] = *reinterpret_cast<const uint32_t *>(&l2);
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < EPL; ++e) {
+                            const float h = tf32_rna(v[uu][e]);
+                            hi[e] = __float_as_uint(h);
+                            lo[e] = __float_as_uint(tf32_rna(v[uu][e] - h));
+                        }
+                    }
+                    st_shared_words<NWL>(dst, hi);
+                    if constexpr (Tr::nparts == 2) st_shared_words<NWL>(dst + B_PART, lo);
+                }
             }
+            if (stop) break;
             fence_proxy_async();
             // stall_first_stage (a test switch) withholds the first stage's signal, so the
             // MMA warp's bounded wait runs out and the CTA takes its abort path
@@ -589,18 +604,21 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue
-        // two groups of four warps; group G owns columns [G*ECOLS, (G+1)*ECOLS) of every tile
+        // four groups of four warps; group G owns columns [G*ECOLS, (G+1)*ECOLS) of every tile
         const int et = threadIdx.x - kEpiWarp0 * 32;   // 0..255
         const int G = et >> 7;
         const int a = et & 127;                        // output node handled in the reduction
         const int q = warp & 3;                        // TMEM lane quarter this warp may read
         const int row = 32 * q + lane;                 // accumulator row (permuted node a')
-        const int bar_id = 1 + 2 * G;                  // named barriers 1 and 3
-        float *sFg = sF + G * ECH * 129;
-        // per column of this group: the dp4a multipliers of its sigma and the byte address of
-        // node 0 of its transpose column; and its target (-1: dead column)
-        int2 *e_wt = s_erec + G * ECOLS;
-        int *e_tgt = reinterpret_cast<int *>(s_erec + NT) + G * ECOLS;
+        const int bar_id = G == 0 ? 1 : 2 + G;         // named barriers 1, 3, 4, 5 (2: producers)
+        // two transpose buffers per group: chunk c (counted across tiles) uses buffer c & 1,
+        // so one barrier per chunk separates its writes from its reads
+        float *sFg = sF + 2 * G * ECH * 129;
+        constexpr int NCHG = ECOLS / ECH;                 // chunks per group and tile
+        // per column of this group, double-buffered by tile: the dp4a multipliers of its sigma
+        // and the byte address of node 0 of its transpose column; and its target (-1: dead)
+        int2 *e_wt0 = s_erec + G * 2 * ECOLS;
+        int *e_tgt0 = reinterpret_cast<int *>(s_erec + 2 * NT) + G * 2 * ECOLS;
         // digits of a' in signed bytes, the other dp4a operand
         const int xd = (row % ell) | ((row / ell % ell) << 8) | ((row / (ell * ell)) << 16);
         const int col_addr = (int)smem_u32(sFg) + (a % ECH) * 129 * 4;   // used by threads a < ECOLS
@@ -617,9 +635,12 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
         }
         for (int t = first; t < last; ++t) {
             const int i = t - first, ab = i % NACC, ak = i / NACC;
+            int2 *e_wt = e_wt0 + (i & 1) * ECOLS;
+            int *e_tgt = e_tgt0 + (i & 1) * ECOLS;
             if (a < ECOLS) {
                 const int2 ga = s_gaff[nxt == -1 ? 0 : rec_g(nxt)];
-                e_wt[a] = make_int2(ga.x, ga.y + col_addr);
+                const int bsel = ((i * NCHG + a / ECH) & 1) * (ECH * 129 * 4);
+                e_wt[a] = make_int2(ga.x, ga.y + col_addr + bsel);
                 e_tgt[a] = (nxt == -1) ? -1 : rec_tgt(nxt);
                 nxt = -1;
                 if (t + 1 < last) {
@@ -662,9 +683,10 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
                     bm = __ballot_sync(0xffffffffu, lane < ECH && tj >= 0 && tj != tp);
                 }
                 // rows a >= n3 of the transpose are never written: read (in bounds) and never added
+                const float *fb = sFg + ((i * NCHG + ch) & 1) * (ECH * 129);
                 float x[ECH];
 #pragma unroll
-                for (int jj = 0; jj < ECH; ++jj) x[jj] = sFg[jj * 129 + a];
+                for (int jj = 0; jj < ECH; ++jj) x[jj] = fb[jj * 129 + a];
 #pragma unroll
                 for (int h = 0; h < ECH; h += 8) {
                     if (((bm >> h) & 0xFFu) == 0u) {
@@ -685,7 +707,6 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
                         acc += x[jj];
                     }
                 }
-                named_bar_sync(bar_id, 128);
             }
         }
         if (a < n3 && cur >= 0) {
@@ -1106,12 +1127,12 @@ template <int KIND>
 size_t tc_smem_bytes(int katoms)
 {
     using Tr = TcTraits<KIND>;
-    constexpr int ECOLS = Tr::NT / 2;
+    constexpr int ECOLS = Tr::NT / kEpiGroups;
     constexpr int ECH = ECOLS < 16 ? ECOLS : 16;
     const size_t b = 2 * (size_t)katoms * Tr::NT * 128 * Tr::nparts;
     const size_t kpad = (size_t)katoms * (128 / Tr::esz);
-    return 1024 + b + 2 * ECH * 129 * sizeof(float) + 48 * kpad * sizeof(int16_t) +
-           (4 * Tr::NT + 48) * sizeof(int2) + 16 * sizeof(uint64_t);
+    return 1024 + b + 2 * kEpiGroups * ECH * 129 * sizeof(float) + 48 * kpad * sizeof(int16_t) +
+           (5 * Tr::NT + 48) * sizeof(int2) + 16 * sizeof(uint64_t);
 }
 
 template <int KIND, int KATOMS>
