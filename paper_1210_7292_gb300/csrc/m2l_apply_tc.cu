@@ -52,7 +52,7 @@ template <> struct TcTraits<TC_BF16X3> {
     static constexpr uint32_t fmt = 1;  // BF16 in the kind::f16 instruction descriptor
 };
 template <> struct TcTraits<TC_TF32X3> {
-    static constexpr int esz = 4, nparts = 2, nprod = 3, NT = 32;
+    static constexpr int esz = 4, nparts = 2, nprod = 3, NT = 64;
     static constexpr uint32_t fmt = 2;
 };
 
