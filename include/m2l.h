@@ -197,6 +197,24 @@ m2l_status m2l_plan_apply(const m2l_plan *plan, const void *in_vectors, void *ou
  * ([nvalid][3]: source index, target index, g, in execution order). */
 m2l_status m2l_plan_query(const m2l_plan *plan, int64_t *counts16, int32_t *records, int64_t *nvalid);
 void m2l_plan_free(m2l_plan *plan);
+/* Re-classify a level into an existing plan (step a3 of Alg. 2, as in
+ * m2l_plan_create), asynchronously on `stream`: no host synchronisation, and
+ * no allocation once the plan's buffers have held a classification of at
+ * least level->nnz entries (the first call after m2l_plan_create allocates its
+ * scratch again).  The plan keeps its direction (adjoint or not) and takes
+ * the level's width.  Plans of different levels may be re-classified and
+ * applied concurrently on different streams; calls on one plan are ordered by
+ * its stream.  Errors: M2L_EINVAL for a null plan or an invalid level (as
+ * m2l_apply_level); bad list entries are reported by m2l_sync_status. */
+m2l_status m2l_plan_classify(m2l_plan *plan, const m2l_level *level, void *stream);
+
+/* Build, on `stream`, the kernel layouts of the operators for `precision`
+ * (the step every first apply after m2l_precompute / m2l_ops_rebuild takes
+ * otherwise): call it before applying one m2l_ops from several streams, so
+ * that no apply builds them concurrently.  Stream-ordered; allocates on its
+ * first call per precision only.  Errors: M2L_EINVAL (null ops, unknown
+ * precision), M2L_EUNSUPPORTED (as the apply would return). */
+m2l_status m2l_ops_prepare(const m2l_ops *ops, int precision, void *stream);
 
 /* Batched apply: nbatch independent (ops, level) problems.  For M2L_FP32 and
  * M2L_FP64 the problems are classified (one plan each) and then applied by ONE

@@ -334,6 +334,28 @@ m2l_status m2l_plan_apply(const m2l_plan *plan, const void *in_vectors, void *ou
     return dispatch(ops, plan->b, in_vectors, out_vectors, precision, out_fp64, scale, (cudaStream_t)stream);
 }
 
+m2l_status m2l_plan_classify(m2l_plan *plan, const m2l_level *level, void *stream)
+{
+    if (!plan) { set_error("null plan"); return M2L_EINVAL; }
+    double scale = 1.0;
+    m2l_status st = check_level(plan->ops, level, &scale);
+    if (st != M2L_OK) return st;
+    st = classify(plan->ops, level, plan->adjoint, plan->b, (cudaStream_t)stream);
+    if (st != M2L_OK) return st;
+    plan->width = level->width;
+    plan->n_out = plan->adjoint ? level->ncells_src : level->ncells_tgt;
+    plan->n_in = plan->adjoint ? level->ncells_tgt : level->ncells_src;
+    return M2L_OK;
+}
+
+m2l_status m2l_ops_prepare(const m2l_ops *ops, int precision, void *stream)
+{
+    if (!ops) { set_error("null ops"); return M2L_EINVAL; }
+    // an apply over no interactions builds the layouts and launches nothing else
+    Buckets empty;
+    return dispatch(ops, empty, nullptr, nullptr, precision, 0, 1.0, (cudaStream_t)stream);
+}
+
 m2l_status m2l_plan_query(const m2l_plan *plan, int64_t *counts16, int32_t *records, int64_t *nvalid)
 {
     if (!plan) { set_error("null plan"); return M2L_EINVAL; }

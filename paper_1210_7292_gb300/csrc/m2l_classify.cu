@@ -56,61 +56,70 @@ __device__ __forceinline__ uint16_t classify_entry(int e, const int32_t *__restr
     return c;
 }
 
-// Class code of every list entry, one thread per entry.
-__global__ void classify_kernel(int nnz, const int32_t *__restrict__ tgt_of, const int32_t *__restrict__ sources,
-                                const int32_t *__restrict__ tgt_ijk, const int32_t *__restrict__ src_ijk, int nsrc,
-                                const uint16_t *__restrict__ lut, uint16_t *__restrict__ code,
-                                int *__restrict__ status)
-{
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += gridDim.x * blockDim.x)
-        code[e] = classify_entry(e, tgt_of, sources, tgt_ijk, src_ijk, nsrc, lut, status);
-}
+constexpr int kSegWarps = kSegEntries / 256;   // warps per segment block (one round of 8 x 32 each)
 
-// One warp per segment of kSegEntries entries: per-class counts of the codes
-// (loads batched eight rounds ahead so that their latencies overlap).
-__global__ void count_kernel(int nnz, int nseg, const uint16_t *__restrict__ code, int32_t *__restrict__ seg_counts)
+// One block per segment of kSegEntries entries, warp w taking entries
+// [w 256, (w+1) 256) of it: the class code of every entry (written for the
+// scatter) and the per-class counts of the segment.
+__global__ void __launch_bounds__(kSegWarps * 32)
+classify_count_kernel(int nnz, int nseg, const int32_t *__restrict__ tgt_of, const int32_t *__restrict__ sources,
+                      const int32_t *__restrict__ tgt_ijk, const int32_t *__restrict__ src_ijk, int nsrc,
+                      const uint16_t *__restrict__ lut, uint16_t *__restrict__ code, int32_t *__restrict__ seg_counts,
+                      int *__restrict__ status)
 {
-    __shared__ int cnt[4][17];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int seg = blockIdx.x * 4 + wib;
-    for (int i = lane; i < 17; i += 32) cnt[wib][i] = 0;
-    __syncwarp();
-    if (seg >= nseg) return;
-    const int e0 = seg * kSegEntries;
-    const int e1 = min(nnz, e0 + kSegEntries);
-    for (int base = e0; base < e1; base += 256) {
-        int cls[8];
+    __shared__ int cnt[kSegWarps][17];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int seg = blockIdx.x;
+    for (int i = threadIdx.x; i < kSegWarps * 17; i += blockDim.x) cnt[i / 17][i % 17] = 0;
+    __syncthreads();
+    const int e0 = seg * kSegEntries + w * 256;
+    const int e1 = min(nnz, seg * kSegEntries + kSegEntries);
+    int cls[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = base + 32 * u + lane;
-            cls[u] = 17;
-            if (e < e1) {
-                const uint16_t c = code[e];
-                cls[u] = (c == 0xFFFF) ? 16 : (c & 0xFF);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const unsigned peers = __match_any_sync(0xffffffffu, cls[u]);
-            if (cls[u] < 17 && lane == __ffs(peers) - 1) cnt[wib][cls[u]] += __popc(peers);
-            __syncwarp();
+    for (int u = 0; u < 8; ++u) {
+        const int e = e0 + 32 * u + lane;
+        cls[u] = 17;
+        if (e < e1) {
+            const uint16_t c = classify_entry(e, tgt_of, sources, tgt_ijk, src_ijk, nsrc, lut, status);
+            code[e] = c;
+            cls[u] = (c == 0xFFFF) ? 16 : (c & 0xFF);
         }
     }
-    for (int i = lane; i < 17; i += 32) seg_counts[(size_t)i * nseg + seg] = cnt[wib][i];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const unsigned peers = __match_any_sync(0xffffffffu, cls[u]);
+        if (cls[u] < 17 && lane == __ffs(peers) - 1) cnt[w][cls[u]] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    if (threadIdx.x < 17) {
+        int sum = 0;
+#pragma unroll
+        for (int k = 0; k < kSegWarps; ++k) sum += cnt[k][threadIdx.x];
+        seg_counts[(size_t)threadIdx.x * nseg + seg] = sum;
+    }
 }
 
-// Single-block exclusive scan of n ints; out[n] = total.
-__global__ void exclusive_scan_kernel(const int32_t *__restrict__ in, int32_t *__restrict__ out, int n)
+// Single-block exclusive scan of n ints; out[n] = total.  Each round covers
+// 8 kScanThreads elements, eight consecutive ones per thread.
+__global__ void __launch_bounds__(kScanThreads) exclusive_scan_kernel(const int32_t *__restrict__ in,
+                                                                      int32_t *__restrict__ out, int n)
 {
     __shared__ int warp_sums[kScanThreads / 32];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int base = 0; base < n; base += kScanThreads) {
-        const int i = base + threadIdx.x;
-        const int v = (i < n) ? in[i] : 0;
-        int incl = v;
+    for (int base = 0; base < n; base += 8 * kScanThreads) {
+        const int i0 = base + 8 * threadIdx.x;
+        int v[8];
+        int tsum = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            v[k] = (i0 + k < n) ? in[i0 + k] : 0;
+            tsum += v[k];
+        }
+        int incl = tsum;
         for (int d = 1; d < 32; d <<= 1) {
             const int u = __shfl_up_sync(0xffffffffu, incl, d);
             if (lane >= d) incl += u;
@@ -123,13 +132,17 @@ __global__ void exclusive_scan_kernel(const int32_t *__restrict__ in, int32_t *_
                 const int u = __shfl_up_sync(0xffffffffu, s, d);
                 if (lane >= d) s += u;
             }
-            warp_sums[lane] = s;  // inclusive over warps
+            warp_sums[lane] = s;   // inclusive over warps
         }
         __syncthreads();
-        const int before = carry + (wid > 0 ? warp_sums[wid - 1] : 0);
-        if (i < n) out[i] = before + incl - v;
+        int run = carry + (wid > 0 ? warp_sums[wid - 1] : 0) + incl - tsum;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (i0 + k < n) out[i0 + k] = run;
+            run += v[k];
+        }
         __syncthreads();
-        if (threadIdx.x == kScanThreads - 1) carry = before + incl;
+        if (threadIdx.x == kScanThreads - 1) carry = run;
         __syncthreads();
     }
     if (threadIdx.x == 0) out[n] = carry;
@@ -143,48 +156,63 @@ __global__ void class_offsets_kernel(int nseg, int nnz, const int32_t *__restric
     if (c == 17) class_off[17] = nnz;
 }
 
-// One warp per segment, in order: stable positions inside each bucket (loads
-// batched eight rounds ahead).
-__global__ void scatter_kernel(int nnz, int nseg, const uint16_t *__restrict__ code,
-                               const int32_t *__restrict__ tgt_of, const int32_t *__restrict__ sources,
-                               const int32_t *__restrict__ seg_pos, int2 *__restrict__ rec)
+// One block per segment, warp w taking entries [w 256, (w+1) 256) of it, in
+// order: the counts of each warp, then stable positions inside each bucket
+// from the segment's position and the counts of the warps before.
+__global__ void __launch_bounds__(kSegWarps * 32)
+scatter_kernel(int nnz, int nseg, const uint16_t *__restrict__ code, const int32_t *__restrict__ tgt_of,
+               const int32_t *__restrict__ sources, const int32_t *__restrict__ seg_pos, int2 *__restrict__ rec)
 {
-    __shared__ int base[4][17];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int seg = blockIdx.x * 4 + wib;
-    if (seg >= nseg) return;
-    for (int i = lane; i < 17; i += 32) base[wib][i] = seg_pos[(size_t)i * nseg + seg];
-    __syncwarp();
-    const int e0 = seg * kSegEntries;
-    const int e1 = min(nnz, e0 + kSegEntries);
+    __shared__ int cnt[kSegWarps][17];
+    __shared__ int base[kSegWarps][17];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int seg = blockIdx.x;
+    for (int i = threadIdx.x; i < kSegWarps * 17; i += blockDim.x) cnt[i / 17][i % 17] = 0;
+    __syncthreads();
+    const int e0 = seg * kSegEntries + w * 256;
+    const int e1 = min(nnz, seg * kSegEntries + kSegEntries);
     const unsigned lt = (1u << lane) - 1u;
-    for (int b = e0; b < e1; b += 256) {
-        int cls[8], src[8], tgt[8];
-        uint16_t cc[8];
+    int cls[8], src[8], tgt[8];
+    uint16_t cc[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = b + 32 * u + lane;
-            cls[u] = 17;
-            cc[u] = 0xFFFF;
-            src[u] = 0;
-            tgt[u] = 0;
-            if (e < e1) {
-                cc[u] = code[e];
-                cls[u] = (cc[u] == 0xFFFF) ? 16 : (cc[u] & 0xFF);
-                src[u] = sources[e];
-                tgt[u] = tgt_of[e];
-            }
+    for (int u = 0; u < 8; ++u) {
+        const int e = e0 + 32 * u + lane;
+        cls[u] = 17;
+        cc[u] = 0xFFFF;
+        src[u] = 0;
+        tgt[u] = 0;
+        if (e < e1) {
+            cc[u] = code[e];
+            cls[u] = (cc[u] == 0xFFFF) ? 16 : (cc[u] & 0xFF);
+            src[u] = sources[e];
+            tgt[u] = tgt_of[e];
         }
+    }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const unsigned peers = __match_any_sync(0xffffffffu, cls[u]);
-            int pos = 0;
-            if (cls[u] < 17) pos = base[wib][cls[u]] + __popc(peers & lt);
-            __syncwarp();
-            if (cls[u] < 17 && lane == __ffs(peers) - 1) base[wib][cls[u]] += __popc(peers);
-            __syncwarp();
-            if (cls[u] < 16) rec[pos] = make_int2(src[u], rec_pack(tgt[u], (int)(cc[u] >> 8)));
+    for (int u = 0; u < 8; ++u) {
+        const unsigned peers = __match_any_sync(0xffffffffu, cls[u]);
+        if (cls[u] < 17 && lane == __ffs(peers) - 1) cnt[w][cls[u]] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    if (threadIdx.x < 17) {
+        int run = seg_pos[(size_t)threadIdx.x * nseg + seg];
+#pragma unroll
+        for (int k = 0; k < kSegWarps; ++k) {
+            base[k][threadIdx.x] = run;
+            run += cnt[k][threadIdx.x];
         }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const unsigned peers = __match_any_sync(0xffffffffu, cls[u]);
+        int pos = 0;
+        if (cls[u] < 17) pos = base[w][cls[u]] + __popc(peers & lt);
+        __syncwarp();
+        if (cls[u] < 17 && lane == __ffs(peers) - 1) base[w][cls[u]] += __popc(peers);
+        __syncwarp();
+        if (cls[u] < 16) rec[pos] = make_int2(src[u], rec_pack(tgt[u], (int)(cc[u] >> 8)));
     }
 }
 
@@ -274,17 +302,16 @@ static m2l_status bucket(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const 
     }
     int32_t *counts = b.seg.as<int32_t>();
     int32_t *pos = counts + 17 * (size_t)nseg + 1;
-    classify_kernel<<<(nnz + 255) / 256, 256, 0, s>>>(nnz, b.tgt_of.as<int32_t>(), sources, tgt_ijk, src_ijk, nsrc,
-                                                     ops->lut.as<uint16_t>(), b.code.as<uint16_t>(), ops->d_status);
-    M2L_LAUNCH_CHECK("classify_kernel");
-    count_kernel<<<(nseg + 3) / 4, 128, 0, s>>>(nnz, nseg, b.code.as<uint16_t>(), counts);
-    M2L_LAUNCH_CHECK("count_kernel");
+    classify_count_kernel<<<nseg, kSegWarps * 32, 0, s>>>(nnz, nseg, b.tgt_of.as<int32_t>(), sources, tgt_ijk,
+                                                           src_ijk, nsrc, ops->lut.as<uint16_t>(),
+                                                           b.code.as<uint16_t>(), counts, ops->d_status);
+    M2L_LAUNCH_CHECK("classify_count_kernel");
     exclusive_scan_kernel<<<1, kScanThreads, 0, s>>>(counts, pos, 17 * nseg);
     M2L_LAUNCH_CHECK("exclusive_scan_kernel");
     class_offsets_kernel<<<1, 32, 0, s>>>(nseg, nnz, pos, b.class_off.as<int32_t>());
     M2L_LAUNCH_CHECK("class_offsets_kernel");
-    scatter_kernel<<<(nseg + 3) / 4, 128, 0, s>>>(nnz, nseg, b.code.as<uint16_t>(), b.tgt_of.as<int32_t>(), sources,
-                                                  pos, b.rec.as<int2>());
+    scatter_kernel<<<nseg, kSegWarps * 32, 0, s>>>(nnz, nseg, b.code.as<uint16_t>(), b.tgt_of.as<int32_t>(), sources,
+                                                    pos, b.rec.as<int2>());
     M2L_LAUNCH_CHECK("scatter_kernel");
     return M2L_OK;
 }
@@ -363,16 +390,14 @@ m2l_status bucket_raw(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const int
     }
     int32_t *counts = seg;
     int32_t *pos = seg + 17 * (size_t)nseg + 1;
-    classify_kernel<<<(nnz + 255) / 256, 256, 0, s>>>(nnz, tgt_of, sources, tgt_ijk, src_ijk, nsrc,
-                                                     ops->lut.as<uint16_t>(), code, ops->d_status);
-    M2L_LAUNCH_CHECK("classify_kernel");
-    count_kernel<<<(nseg + 3) / 4, 128, 0, s>>>(nnz, nseg, code, counts);
-    M2L_LAUNCH_CHECK("count_kernel");
+    classify_count_kernel<<<nseg, kSegWarps * 32, 0, s>>>(nnz, nseg, tgt_of, sources, tgt_ijk, src_ijk, nsrc,
+                                                           ops->lut.as<uint16_t>(), code, counts, ops->d_status);
+    M2L_LAUNCH_CHECK("classify_count_kernel");
     exclusive_scan_kernel<<<1, kScanThreads, 0, s>>>(counts, pos, 17 * nseg);
     M2L_LAUNCH_CHECK("exclusive_scan_kernel");
     class_offsets_kernel<<<1, 32, 0, s>>>(nseg, nnz, pos, class_off);
     M2L_LAUNCH_CHECK("class_offsets_kernel");
-    scatter_kernel<<<(nseg + 3) / 4, 128, 0, s>>>(nnz, nseg, code, tgt_of, sources, pos, rec);
+    scatter_kernel<<<nseg, kSegWarps * 32, 0, s>>>(nnz, nseg, code, tgt_of, sources, pos, rec);
     M2L_LAUNCH_CHECK("scatter_kernel");
     return M2L_OK;
 }

@@ -23,7 +23,7 @@ constexpr int kMaxEll = 8;
 constexpr int kNumSym = 16;     // |T_sym| for the bbFMM (Sec. 4.2.1)
 constexpr int kNumPerm = 48;    // signed axis permutations
 constexpr int kTgtBits = 26;    // record packing: tgt | g << 26
-constexpr int kSegEntries = 2048;  // entries per warp segment of the stable bucketing
+constexpr int kSegEntries = 2048;  // entries per block segment of the stable bucketing
 
 // Bucketed record .y field: target index in the low 26 bits, permutation
 // index g (< 48) in the high 6 bits.  Unpacked with unsigned shifts: g >= 32

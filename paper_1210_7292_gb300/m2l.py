@@ -65,6 +65,8 @@ def lib():
             "m2l_plan_create": [P, ctypes.POINTER(m2l_level), I, P, ctypes.POINTER(P)],
             "m2l_plan_apply": [P, P, P, I, I, P],
             "m2l_plan_query": [P, P, P, P],
+            "m2l_plan_classify": [P, ctypes.POINTER(m2l_level), P],
+            "m2l_ops_prepare": [P, I, P],
             "m2l_apply_batch": [P, ctypes.POINTER(m2l_level), P, P, I, I, I, P],
             "m2l_build_lists": [I, P, I, P, P, P, P, P],
             "m2l_apply_level_noalloc": [P, ctypes.POINTER(m2l_level), P, P, P],
@@ -257,7 +259,9 @@ def m2l_plan_create(ops: Ops, level: Level, adjoint=False, stream=None) -> Plan:
                                                     _stream_ptr(stream), ctypes.byref(h)))
     s = level.struct
     n_in, n_out = (s.ncells_tgt, s.ncells_src) if adjoint else (s.ncells_src, s.ncells_tgt)
-    return Plan(h, ops, n_in, n_out)
+    plan = Plan(h, ops, n_in, n_out)
+    plan.adjoint = bool(adjoint)
+    return plan
 
 
 def m2l_plan_apply(plan: Plan, vin, vout, precision="fp32", out_fp64=False, stream=None):
@@ -266,6 +270,21 @@ def m2l_plan_apply(plan: Plan, vin, vout, precision="fp32", out_fp64=False, stre
     _check("m2l_plan_apply", lib().m2l_plan_apply(plan.handle, _dev_ptr(vin, tin, "input vectors"),
                                                   _dev_ptr(vout, tout, "output vectors"), p,
                                                   int(bool(out_fp64)), _stream_ptr(stream)))
+
+
+def m2l_plan_classify(plan: Plan, level: Level, stream=None):
+    """Re-classify `level` into `plan` on `stream` (no host synchronisation)."""
+    _check("m2l_plan_classify", lib().m2l_plan_classify(plan.handle, ctypes.byref(level.struct),
+                                                        _stream_ptr(stream)))
+    s = level.struct
+    plan.n_in, plan.n_out = ((s.ncells_tgt, s.ncells_src) if getattr(plan, "adjoint", False)
+                             else (s.ncells_src, s.ncells_tgt))
+    plan.level = level   # the level's device arrays must outlive the stream's use of them
+
+
+def m2l_ops_prepare(ops: Ops, precision="fp32", stream=None):
+    """Build the operators' kernel layouts for `precision` on `stream`."""
+    _check("m2l_ops_prepare", lib().m2l_ops_prepare(ops.handle, PRECISIONS[precision], _stream_ptr(stream)))
 
 
 def m2l_plan_query(plan: Plan):

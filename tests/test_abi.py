@@ -58,6 +58,8 @@ def test_null_handles_rejected(lib):
     assert lib.m2l_plan_apply(None, None, None, 1, 0, None) == m2l.M2L_EINVAL
     assert lib.m2l_apply_level(None, None, None, None, 1, 0, None) == m2l.M2L_EINVAL
     assert lib.m2l_build_lists(-1, None, 0, None, None, None, None, None) == m2l.M2L_EINVAL
+    assert lib.m2l_plan_classify(None, None, None) == m2l.M2L_EINVAL
+    assert lib.m2l_ops_prepare(None, 1, None) == m2l.M2L_EINVAL
     lib.m2l_ops_free(None)
     lib.m2l_plan_free(None)
 
