@@ -100,10 +100,10 @@ classify_count_kernel(int nnz, int nseg, const int32_t *__restrict__ tgt_of, con
     }
 }
 
-// Single-block exclusive scan of n ints; out[n] = total.  Each round covers
-// 8 kScanThreads elements, eight consecutive ones per thread.
-__global__ void __launch_bounds__(kScanThreads) exclusive_scan_kernel(const int32_t *__restrict__ in,
-                                                                      int32_t *__restrict__ out, int n)
+// Exclusive scan of n ints by one block of kScanThreads threads; returns the
+// total to every thread.  Each round covers 8 kScanThreads elements, eight
+// consecutive ones per thread.
+__device__ int block_exclusive_scan(const int32_t *__restrict__ in, int32_t *__restrict__ out, int n)
 {
     __shared__ int warp_sums[kScanThreads / 32];
     __shared__ int carry;
@@ -145,15 +145,38 @@ __global__ void __launch_bounds__(kScanThreads) exclusive_scan_kernel(const int3
         if (threadIdx.x == kScanThreads - 1) carry = run;
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[n] = carry;
+    return carry;
 }
 
-__global__ void class_offsets_kernel(int nseg, int nnz, const int32_t *__restrict__ pos,
+// Single-block exclusive scan of n ints; out[n] = total.
+__global__ void __launch_bounds__(kScanThreads) exclusive_scan_kernel(const int32_t *__restrict__ in,
+                                                                      int32_t *__restrict__ out, int n)
+{
+    const int total = block_exclusive_scan(in, out, n);
+    if (threadIdx.x == 0) out[n] = total;
+}
+
+// Per-class positions of the segments: block c scans row c of counts [17][nseg]
+// into pos, then stores the row total in counts[c nseg] (the row is read by now).
+__global__ void __launch_bounds__(kScanThreads) row_scan_kernel(int32_t *__restrict__ counts,
+                                                                int32_t *__restrict__ pos, int nseg)
+{
+    const int c = blockIdx.x;
+    const int total = block_exclusive_scan(counts + (size_t)c * nseg, pos + (size_t)c * nseg, nseg);
+    if (threadIdx.x == 0) counts[(size_t)c * nseg] = total;
+}
+
+// Bucket starts from the class totals left by row_scan_kernel in counts[c nseg].
+__global__ void class_offsets_kernel(int nseg, int nnz, const int32_t *__restrict__ counts,
                                      int32_t *__restrict__ class_off)
 {
-    const int c = threadIdx.x;
-    if (c < 17) class_off[c] = pos[(size_t)c * nseg];
-    if (c == 17) class_off[17] = nnz;
+    if (threadIdx.x != 0) return;
+    int run = 0;
+    for (int c = 0; c < 17; ++c) {
+        class_off[c] = run;
+        run += counts[(size_t)c * nseg];
+    }
+    class_off[17] = nnz;
 }
 
 // One block per segment, warp w taking entries [w 256, (w+1) 256) of it, in
@@ -161,7 +184,8 @@ __global__ void class_offsets_kernel(int nseg, int nnz, const int32_t *__restric
 // from the segment's position and the counts of the warps before.
 __global__ void __launch_bounds__(kSegWarps * 32)
 scatter_kernel(int nnz, int nseg, const uint16_t *__restrict__ code, const int32_t *__restrict__ tgt_of,
-               const int32_t *__restrict__ sources, const int32_t *__restrict__ seg_pos, int2 *__restrict__ rec)
+               const int32_t *__restrict__ sources, const int32_t *__restrict__ seg_pos,
+               const int32_t *__restrict__ class_off, int2 *__restrict__ rec)
 {
     __shared__ int cnt[kSegWarps][17];
     __shared__ int base[kSegWarps][17];
@@ -196,7 +220,7 @@ scatter_kernel(int nnz, int nseg, const uint16_t *__restrict__ code, const int32
     }
     __syncthreads();
     if (threadIdx.x < 17) {
-        int run = seg_pos[(size_t)threadIdx.x * nseg + seg];
+        int run = class_off[threadIdx.x] + seg_pos[(size_t)threadIdx.x * nseg + seg];
 #pragma unroll
         for (int k = 0; k < kSegWarps; ++k) {
             base[k][threadIdx.x] = run;
@@ -306,12 +330,12 @@ static m2l_status bucket(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const 
                                                            src_ijk, nsrc, ops->lut.as<uint16_t>(),
                                                            b.code.as<uint16_t>(), counts, ops->d_status);
     M2L_LAUNCH_CHECK("classify_count_kernel");
-    exclusive_scan_kernel<<<1, kScanThreads, 0, s>>>(counts, pos, 17 * nseg);
-    M2L_LAUNCH_CHECK("exclusive_scan_kernel");
-    class_offsets_kernel<<<1, 32, 0, s>>>(nseg, nnz, pos, b.class_off.as<int32_t>());
+    row_scan_kernel<<<17, kScanThreads, 0, s>>>(counts, pos, nseg);
+    M2L_LAUNCH_CHECK("row_scan_kernel");
+    class_offsets_kernel<<<1, 32, 0, s>>>(nseg, nnz, counts, b.class_off.as<int32_t>());
     M2L_LAUNCH_CHECK("class_offsets_kernel");
     scatter_kernel<<<nseg, kSegWarps * 32, 0, s>>>(nnz, nseg, b.code.as<uint16_t>(), b.tgt_of.as<int32_t>(), sources,
-                                                    pos, b.rec.as<int2>());
+                                                    pos, b.class_off.as<int32_t>(), b.rec.as<int2>());
     M2L_LAUNCH_CHECK("scatter_kernel");
     return M2L_OK;
 }
@@ -393,11 +417,11 @@ m2l_status bucket_raw(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const int
     classify_count_kernel<<<nseg, kSegWarps * 32, 0, s>>>(nnz, nseg, tgt_of, sources, tgt_ijk, src_ijk, nsrc,
                                                            ops->lut.as<uint16_t>(), code, counts, ops->d_status);
     M2L_LAUNCH_CHECK("classify_count_kernel");
-    exclusive_scan_kernel<<<1, kScanThreads, 0, s>>>(counts, pos, 17 * nseg);
-    M2L_LAUNCH_CHECK("exclusive_scan_kernel");
-    class_offsets_kernel<<<1, 32, 0, s>>>(nseg, nnz, pos, class_off);
+    row_scan_kernel<<<17, kScanThreads, 0, s>>>(counts, pos, nseg);
+    M2L_LAUNCH_CHECK("row_scan_kernel");
+    class_offsets_kernel<<<1, 32, 0, s>>>(nseg, nnz, counts, class_off);
     M2L_LAUNCH_CHECK("class_offsets_kernel");
-    scatter_kernel<<<nseg, kSegWarps * 32, 0, s>>>(nnz, nseg, code, tgt_of, sources, pos, rec);
+    scatter_kernel<<<nseg, kSegWarps * 32, 0, s>>>(nnz, nseg, code, tgt_of, sources, pos, class_off, rec);
     M2L_LAUNCH_CHECK("scatter_kernel");
     return M2L_OK;
 }
