@@ -17,6 +17,7 @@ value = far-field interactions of levels 2..5 / step time, summed over ranks.
 from __future__ import annotations
 
 import argparse
+import platform
 import json
 import os
 import statistics
@@ -160,7 +161,7 @@ def max_over_ranks(world, value, device):
 
 
 # --------------------------------------------------------------------------------------------
-def cpu_oracle_sample(ntargets=2048, seed=11):
+def cpu_oracle_sample(ntargets=2048, seed=11, with_locals=False):
     """The oracle, as it stands, on a bounded sample of the level-5 workload:
     the 316 directly assembled operators plus the cell-by-cell M2L of
     `ntargets` random level-5 target cells with their full lists."""
@@ -175,13 +176,80 @@ def cpu_oracle_sample(ntargets=2048, seed=11):
     off, src = oracle.interaction_lists(cells[samp], cells)
     t0 = time.perf_counter()
     ops = oracle.operator_table(ELL, KERNEL, 0.0, 5)
-    oracle.m2l_apply(ops, cells[samp], cells, off, src, w)
+    loc = oracle.m2l_apply(ops, cells[samp], cells, off, src, w)
     dt = time.perf_counter() - t0
     nint = int(off[-1])
-    return {"value": nint / dt, "unit": "interactions/s", "cores": 1, "kind": "oracle",
-            "sample": "%d random level-5 target cells (%d interactions) of the workload, 316 operators "
-                      "assembled directly, single-threaded C loops, %.1f s" % (ntargets, nint, dt),
-            "gflops": nint * FLOPS_PER_INTERACTION / dt / 1e9}
+    out = {"value": nint / dt, "unit": "interactions/s", "cores": 1, "kind": "oracle",
+           "sample": "%d random level-5 target cells (%d interactions) of the workload, 316 operators "
+                     "assembled directly, single-threaded C loops, %.1f s" % (ntargets, nint, dt),
+           "gflops": nint * FLOPS_PER_INTERACTION / dt / 1e9}
+    if with_locals:
+        return out, loc
+    return out
+
+
+def host_info():
+    """Host cores and CPU model, for the CPU baselines."""
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_count": os.cpu_count(), "model": model, "machine": platform.machine()}
+
+
+def cpu_nablk_sample(ntargets=2048, seed=11, ref=None):
+    """The paper's blocked method on the host cores (a paper-style CPU baseline, not
+    the oracle): per sampled level-5 target cell the full list, classified by the 16
+    unique operators (Sec. 4.2.1), gathered and permuted per class, one BLAS matrix
+    product per class (Sec. 4.2.3, NumPy's multithreaded BLAS), un-permuted and
+    summed per target.  Operators and tables are built from the oracle's definitions
+    inside the timed region, as the GPU step rebuilds them."""
+    import numpy as np
+
+    import oracle
+    from paper_1210_7292_gb300 import synth
+    n3 = ELL ** 3
+    cells = synth.full_grid(5)
+    w = synth.gaussian_vectors(len(cells), n3, seed=SEED)
+    rng = np.random.default_rng(seed)
+    samp = np.sort(rng.choice(len(cells), ntargets, replace=False))
+    off, src = oracle.interaction_lists(cells[samp], cells)
+    tgt = np.repeat(np.arange(len(samp)), np.diff(off))
+    t0 = time.perf_counter()
+    kp = np.stack([oracle.operator_for_t(ELL, KERNEL, 0.0, 5, t) for t in oracle.t_sym_list()])
+    sig = oracle.sigma_tables(ELL)
+    lut = oracle.lut343().astype(np.int64)
+    t = cells[samp][tgt] - cells[src]
+    code = lut[(t[:, 0] + 3) + 7 * (t[:, 1] + 3) + 49 * (t[:, 2] + 3)]
+    p, g = code & 0xFF, code >> 8
+    order = np.argsort(p, kind="stable")
+    bounds = np.searchsorted(p[order], np.arange(17))
+    loc = np.zeros((len(samp), n3))
+    for q in range(16):
+        sel = order[bounds[q]:bounds[q + 1]]
+        if len(sel) == 0:
+            continue
+        sg = sig[g[sel]]
+        wp = np.empty((len(sel), n3))
+        np.put_along_axis(wp, sg, w[src[sel]], axis=1)       # W[sigma(b)] = w[b]
+        f = np.take_along_axis(wp @ kp[q].T, sg, axis=1)     # F = K_p W; f[a] = F[sigma(a)]
+        tq = tgt[sel]                                        # ascending within the class
+        starts = np.flatnonzero(np.r_[True, tq[1:] != tq[:-1]])
+        loc[tq[starts]] += np.add.reduceat(f, starts, axis=0)
+    dt = time.perf_counter() - t0
+    nint = int(off[-1])
+    out = {"value": nint / dt, "unit": "interactions/s", "cores": os.cpu_count(),
+           "kind": "paper-style blocked CPU (NumPy BLAS, all host cores; not the oracle)",
+           "sample": "the same %d level-5 target cells (%d interactions), %.2f s" % (ntargets, nint, dt),
+           "gflops": nint * FLOPS_PER_INTERACTION / dt / 1e9}
+    if ref is not None:
+        out["rel_l2_vs_oracle"] = float(np.linalg.norm(loc - ref) / np.linalg.norm(ref))
+    return out
 
 
 def run_reference(args):
@@ -439,7 +507,11 @@ def run_ours(args):
                 extra[p] = res
             except m2l.M2LError as e:
                 extra[p] = {"unavailable": str(e)}
-    cpu = cpu_oracle_sample() if (rank == 0 and world == 1 and not args.quick) else None
+    cpu = None
+    if rank == 0 and world == 1 and not args.quick:
+        cpu, ref_loc = cpu_oracle_sample(with_locals=True)
+        cpu["host"] = host_info()
+        cpu["nablk"] = cpu_nablk_sample(ref=ref_loc)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
