@@ -431,8 +431,10 @@ def roofline(precision, achieved_tflops, peaks, src_kind):
             peak, how = bf / 3.0, "bf16 sustained (%s) / 3 products" % src_kind
         else:
             peak, how = bf * NOMINAL["tf32"] / NOMINAL["bf16"] / 3.0, "bf16 sustained (%s) x 1.1/2.25 / 3" % src_kind
+    nprod = 3 if precision in ("bf16x3", "tf32x3") else 1   # tensor products per algorithmic one
     return {"bound": bound, "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved_tflops / peak, "traffic": traffic_for(kname), "kernel": kname, "peak_source": how,
+            "executed_tflops": achieved_tflops * nprod, "products_per_flop": nprod,
             "flops_per_launch": FLOPS_PER_INTERACTION * full_interactions(5),
             "flop_convention": "algorithmic 2*ell^6 per interaction, level-5 launch"}
 
