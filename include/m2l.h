@@ -247,6 +247,43 @@ m2l_status m2l_batch_info(const m2l_batch *batch, int *tile_width, int64_t *tile
 void m2l_batch_free(m2l_batch *batch);
 
 /* ---------------------------------------------------------------------
+ * The bbFMM matvec around the M2L translation (Sec. 2.1.1, Eqs. (5)-(8)):
+ * P2M at the leaves, M2M up to level 2, the symmetry-blocked M2L at every
+ * level 2..leaf, L2L down to the leaves, then L2P plus the direct near field
+ * over the <= 27 neighbour leaves (Eq. (1) restricted to them, exact
+ * coincidences skipped).  Uniform-depth octree on [lo, lo + domain_width)^3
+ * with empty cells pruned; particles are binned into half-open leaf cells
+ * (top face clamped); the cells of a level are sorted by linear index (x
+ * fastest), as are the lists of m2l_build_lists.  The paper leaves these
+ * passes unchanged; they surround the path it optimises.
+ *
+ * m2l_fmm_create: ops[L - 2] are the operators of level L = 2..leaf_level
+ *   (one m2l_ops for all levels when the kernel is homogeneous; a
+ *   non-homogeneous kernel needs one set per level width); they must share
+ *   kernel and order (ell <= 8).  xyz: device [n][3], double if fp64 != 0,
+ *   else float.  Builds the tree, the kept cells of every level, their
+ *   interaction lists and one M2L plan per level; synchronous; allocates
+ *   everything it keeps.  leaf_level in [2, 8].
+ * m2l_fmm_evaluate: charges (device [n]) -> potentials (device [n], written,
+ *   input order), same type as xyz; precision M2L_FP64 for an fp64 FMM, one
+ *   of the other precisions for an FP32 one.  Stream-ordered; no allocation.
+ * m2l_fmm_query: host copies of level L's cell coordinates ([ncells][3]),
+ *   multipoles W and locals F ([ncells][ell^3], the FMM's type; F includes
+ *   the L2L of the parents) after an evaluate; NULL skips one.  Synchronous.
+ * m2l_fmm_info: leaf level and, per level 0..8, kept cells and list entries.
+ * Errors: M2L_EINVAL (bad arguments, precision not matching the FMM's type),
+ * M2L_EUNSUPPORTED (ell > 8 or level width beyond the operators'), and those
+ * of m2l_plan_create / m2l_plan_apply. */
+typedef struct m2l_fmm m2l_fmm;
+m2l_status m2l_fmm_create(const m2l_ops *const *ops, int n_particles, const void *xyz, int fp64,
+                          int leaf_level, double lo, double domain_width, void *stream, m2l_fmm **out);
+m2l_status m2l_fmm_evaluate(const m2l_fmm *fmm, const void *xyz, const void *charges, void *potentials,
+                            int precision, void *stream);
+m2l_status m2l_fmm_query(const m2l_fmm *fmm, int level, int32_t *host_ijk, void *host_W, void *host_F);
+m2l_status m2l_fmm_info(const m2l_fmm *fmm, int *leaf_level, int64_t *ncells9, int64_t *nnz9);
+void m2l_fmm_free(m2l_fmm *fmm);
+
+/* ---------------------------------------------------------------------
  * Interaction lists (Sec. 3.2, Alg. 1 for asymptotically smooth kernels):
  * Y is in the list of X when their parents are neighbours,
  * |floor(X/2) - floor(Y/2)|_inf <= 1, and |X - Y|_inf >= 2.  Sources of a

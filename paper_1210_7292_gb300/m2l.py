@@ -66,6 +66,10 @@ def lib():
             "m2l_plan_apply": [P, P, P, I, I, P],
             "m2l_plan_query": [P, P, P, P],
             "m2l_plan_classify": [P, ctypes.POINTER(m2l_level), P],
+            "m2l_fmm_create": [P, I, P, I, I, D, D, P, ctypes.POINTER(P)],
+            "m2l_fmm_evaluate": [P, P, P, P, I, P],
+            "m2l_fmm_query": [P, I, P, P, P],
+            "m2l_fmm_info": [P, P, P, P],
             "m2l_ops_prepare": [P, I, P],
             "m2l_apply_batch": [P, ctypes.POINTER(m2l_level), P, P, I, I, I, P],
             "m2l_build_lists": [I, P, I, P, P, P, P, P],
@@ -86,6 +90,8 @@ def lib():
         L.m2l_plan_free.restype = None
         L.m2l_batch_free.argtypes = [P]
         L.m2l_batch_free.restype = None
+        L.m2l_fmm_free.argtypes = [P]
+        L.m2l_fmm_free.restype = None
         L.m2l_last_error.argtypes = []
         L.m2l_last_error.restype = ctypes.c_char_p
         L.m2l_launch_count.argtypes = []
@@ -390,3 +396,75 @@ def m2l_last_error() -> str:
 
 def m2l_launch_count() -> int:
     return int(lib().m2l_launch_count())
+
+
+class FMM:
+    """A bbFMM matvec (tree, per-level lists and M2L plans) built by m2l_fmm_create."""
+
+    def __init__(self, handle, ops_list, n, fp64, ell, leaf):
+        self.handle, self.ops_list, self.n, self.fp64, self.ell, self.leaf = handle, ops_list, n, fp64, ell, leaf
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.m2l_fmm_free(h)
+
+
+def m2l_fmm_create(ops, xyz, leaf_level, lo=-1.0, domain_width=2.0, stream=None) -> FMM:
+    """ops: one Ops for every level (homogeneous kernel) or a dict / list by level
+    2..leaf_level; xyz: device [n, 3] float64 or float32."""
+    import torch
+    if isinstance(ops, Ops):
+        ops_list = [ops] * (leaf_level - 1)
+    elif isinstance(ops, dict):
+        ops_list = [ops[L] for L in range(2, leaf_level + 1)]
+    else:
+        ops_list = list(ops)
+    if len(ops_list) != leaf_level - 1:
+        raise ValueError("need operators for levels 2..%d" % leaf_level)
+    fp64 = xyz.dtype == torch.float64
+    if xyz.dtype not in (torch.float64, torch.float32) or xyz.dim() != 2 or xyz.shape[1] != 3:
+        raise ValueError("xyz must be a [n, 3] float64 or float32 device tensor")
+    arr = (ctypes.c_void_p * len(ops_list))(*[o.handle.value for o in ops_list])
+    h = ctypes.c_void_p()
+    _check("m2l_fmm_create", lib().m2l_fmm_create(arr, xyz.shape[0], _dev_ptr(xyz, xyz.dtype, "xyz"), int(fp64),
+                                                  int(leaf_level), float(lo), float(domain_width),
+                                                  _stream_ptr(stream), ctypes.byref(h)))
+    return FMM(h, ops_list, xyz.shape[0], fp64, ops_list[0].ell, leaf_level)
+
+
+def m2l_fmm_evaluate(fmm: FMM, xyz, charges, potentials, precision=None, stream=None):
+    """potentials[i] = the FMM's approximation of sum_j K(x_i, x_j) q_j (j != i)."""
+    import torch
+    dt = torch.float64 if fmm.fp64 else torch.float32
+    if precision is None:
+        precision = "fp64" if fmm.fp64 else "fp32"
+    for t, what in ((xyz, "xyz"), (charges, "charges"), (potentials, "potentials")):
+        if t.shape[0] != fmm.n:
+            raise ValueError("%s has %d rows, the FMM %d particles" % (what, t.shape[0], fmm.n))
+    _check("m2l_fmm_evaluate", lib().m2l_fmm_evaluate(fmm.handle, _dev_ptr(xyz, dt, "xyz"),
+                                                      _dev_ptr(charges, dt, "charges"),
+                                                      _dev_ptr(potentials, dt, "potentials"),
+                                                      PRECISIONS[precision], _stream_ptr(stream)))
+
+
+def m2l_fmm_info(fmm: FMM):
+    """(leaf level, kept cells per level [9], list entries per level [9])."""
+    leaf = ctypes.c_int()
+    nc = np.zeros(9, dtype=np.int64)
+    nz = np.zeros(9, dtype=np.int64)
+    _check("m2l_fmm_info", lib().m2l_fmm_info(fmm.handle, ctypes.byref(leaf), nc.ctypes.data, nz.ctypes.data))
+    return leaf.value, nc, nz
+
+
+def m2l_fmm_query(fmm: FMM, level: int):
+    """Host (ijk [ncells, 3] int32, W [ncells, ell^3], F [ncells, ell^3]) of a level."""
+    _, nc, _ = m2l_fmm_info(fmm)
+    n = int(nc[level])
+    dt = np.float64 if fmm.fp64 else np.float32
+    ijk = np.zeros((max(n, 1), 3), dtype=np.int32)
+    W = np.zeros((max(n, 1), fmm.ell ** 3), dtype=dt)
+    F = np.zeros((max(n, 1), fmm.ell ** 3), dtype=dt)
+    _check("m2l_fmm_query", lib().m2l_fmm_query(fmm.handle, int(level), ijk.ctypes.data, W.ctypes.data,
+                                                F.ctypes.data))
+    return ijk[:n], W[:n], F[:n]
