@@ -439,6 +439,40 @@ def roofline(precision, achieved_tflops, peaks, src_kind):
             "flop_convention": "algorithmic 2*ell^6 per interaction, level-5 launch"}
 
 
+def fmm_matvec(m2l, device, precision, reps=5):
+    """The whole bbFMM matvec of the workload's particles on the GPU
+    (m2l_fmm_evaluate: P2M, M2M, M2L at levels 2-5, L2L, L2P and near field);
+    set-up (tree, lists, plans) timed apart."""
+    import torch
+
+    from paper_1210_7292_gb300 import synth
+    pts, q = synth.uniform_cube(N_PARTICLES, seed=SEED)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    xyz = torch.from_numpy(pts).to(device, dt)
+    qq = torch.from_numpy(q).to(device, dt)
+    ops = m2l.m2l_precompute(m2l.M2L_K_INV_R, ELL)
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    fmm = m2l.m2l_fmm_create(ops, xyz, max(LEVELS))
+    setup_ms = 1e3 * (time.perf_counter() - t0)
+    phi = torch.zeros(N_PARTICLES, dtype=dt, device=device)
+    for _ in range(2):
+        m2l.m2l_fmm_evaluate(fmm, xyz, qq, phi, precision)
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        m2l.m2l_fmm_evaluate(fmm, xyz, qq, phi, precision)
+        e1.record()
+        torch.cuda.synchronize(device)
+        ts.append(e0.elapsed_time(e1))
+    _, ncells, nnz = m2l.m2l_fmm_info(fmm)
+    return {"ms": statistics.median(ts), "setup_ms": setup_ms, "particles": N_PARTICLES,
+            "leaf_level": max(LEVELS), "ell": ELL, "m2l_precision": precision,
+            "m2l_interactions": int(nnz.sum()), "leaf_cells": int(ncells[max(LEVELS)]),
+            "note": "P2M, M2M, M2L (levels 2-5), L2L, L2P and near field, particles resident on the GPU"}
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_setup(args)
@@ -509,6 +543,7 @@ def run_ours(args):
                 extra[p] = res
             except m2l.M2LError as e:
                 extra[p] = {"unavailable": str(e)}
+    fmm = fmm_matvec(m2l, device, prec) if (rank == 0 and not args.quick and prec != "fp64") else None
     cpu = None
     if rank == 0 and world == 1 and not args.quick:
         cpu, ref_loc = cpu_oracle_sample(with_locals=True)
@@ -530,6 +565,7 @@ def run_ours(args):
                 "e2e": {"value": e2e_val, "unit": "interactions/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches,
+                "fmm_matvec": fmm,
                 "clocks": clk,
                 "precisions": extra}
         print(json.dumps(line), flush=True)
