@@ -41,6 +41,23 @@ __device__ __forceinline__ T kernel_of_r2(int kind, T c, T r2)
     return T(1) / sqrt(r2 + c * c);
 }
 
+// FP32: the hardware reciprocal square root (within a few ulp, far below the
+// FMM's own error) instead of a division by a square root.
+template <>
+__device__ __forceinline__ float kernel_of_r2<float>(int kind, float c, float r2)
+{
+    if (kind == M2L_K_INV_R) return rsqrtf(r2);
+    if (kind == M2L_K_INV_R4) {
+        const float r = rsqrtf(r2);
+        const float r2i = r * r;
+        return r2i * r2i;
+    }
+    return rsqrtf(r2 + c * c);
+}
+
+constexpr int kP2PThreads = 64;     // targets per pass of a near-field block
+constexpr int kP2PChunk = 1024;     // sources staged per chunk
+
 // Leaf cell of every particle (binned in double, as the cells are half-open
 // with the top face clamped) and the particle count per dense leaf cell.
 template <typename T>
@@ -238,17 +255,18 @@ l2l_kernel(int ell, int ncells, const int32_t *__restrict__ ijk, int parent_side
 
 // L2P (Eq. (8)) plus the direct near field over the <= 27 neighbour leaves (Eq. (1)
 // restricted to them, exact coincidences skipped): one block per leaf, one thread
-// per target particle, sources staged in shared memory.  Potentials are written
-// in the particles' input order.
+// per target particle; the sources of all neighbours, concatenated, are staged in
+// shared memory in chunks.  Potentials are written in the particles' input order.
 template <typename T>
-__global__ void __launch_bounds__(kFmmThreads)
+__global__ void __launch_bounds__(kP2PThreads)
 l2p_p2p_kernel(int ell, int kind, double c, int ncells, const int32_t *__restrict__ ijk, int side,
                const int32_t *__restrict__ start, const int32_t *__restrict__ perm, const T *__restrict__ xyz,
                const T *__restrict__ q, double lo, double w, const T *__restrict__ xi, const T *__restrict__ inv_den,
                const T *__restrict__ F, T *__restrict__ phi)
 {
     __shared__ T sF[kMaxN3];
-    __shared__ T sx[kFmmThreads][4];
+    __shared__ T sx[kP2PChunk][4];
+    __shared__ int nb_start[27], nb_pre[28];
     const int cid = blockIdx.x;
     if (cid >= ncells) return;
     const int n3 = ell * ell * ell;
@@ -256,15 +274,35 @@ l2p_p2p_kernel(int ell, int kind, double c, int ncells, const int32_t *__restric
     const int l = ci + side * (cj + side * ck);
     const int j0 = start[l], j1 = start[l + 1];
     for (int i = threadIdx.x; i < n3; i += blockDim.x) sF[i] = F[(size_t)cid * n3 + i];
+    if (threadIdx.x == 0) {
+        // the neighbour leaves' particle ranges, as one concatenated source list
+        int run = 0, k = 0;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx, ++k) {
+                    const int ni = ci + dx, nj = cj + dy, nk = ck + dz;
+                    int s0 = 0, n = 0;
+                    if (ni >= 0 && nj >= 0 && nk >= 0 && ni < side && nj < side && nk < side) {
+                        const int nl = ni + side * (nj + side * nk);
+                        s0 = start[nl];
+                        n = start[nl + 1] - s0;
+                    }
+                    nb_start[k] = s0;
+                    nb_pre[k] = run;
+                    run += n;
+                }
+        nb_pre[27] = run;
+    }
+    __syncthreads();
+    const int nsrc = nb_pre[27];
     const T ctr[3] = {T(lo + w * (ci + 0.5)), T(lo + w * (cj + 0.5)), T(lo + w * (ck + 0.5))};
     const T half = T(0.5 * w);
     const T cc = T(c);
-    for (int tb = j0; tb < j1; tb += kFmmThreads) {
+    for (int tb = j0; tb < j1; tb += kP2PThreads) {
         const int it = tb + threadIdx.x;
         const bool live = it < j1;
         const int p = live ? perm[it] : 0;
         const T x0 = live ? xyz[3 * p] : T(0), x1 = live ? xyz[3 * p + 1] : T(0), x2 = live ? xyz[3 * p + 2] : T(0);
-        __syncthreads();
         T f = T(0);
         if (live) {
             T L0[8], L1[8], L2[8];
@@ -282,34 +320,29 @@ l2p_p2p_kernel(int ell, int kind, double c, int ncells, const int32_t *__restric
             }
         }
         T near = T(0);
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int ni = ci + dx, nj = cj + dy, nk = ck + dz;
-                    if (ni < 0 || nj < 0 || nk < 0 || ni >= side || nj >= side || nk >= side) continue;
-                    const int nl = ni + side * (nj + side * nk);
-                    const int s0 = start[nl], s1 = start[nl + 1];
-                    for (int sb = s0; sb < s1; sb += kFmmThreads) {
-                        __syncthreads();
-                        const int js = sb + threadIdx.x;
-                        if (js < s1) {
-                            const int ps = perm[js];
-                            sx[threadIdx.x][0] = xyz[3 * ps];
-                            sx[threadIdx.x][1] = xyz[3 * ps + 1];
-                            sx[threadIdx.x][2] = xyz[3 * ps + 2];
-                            sx[threadIdx.x][3] = q[ps];
-                        }
-                        __syncthreads();
-                        if (live) {
-                            const int ns = min(kFmmThreads, s1 - sb);
-                            for (int jj = 0; jj < ns; ++jj) {
-                                const T d0 = x0 - sx[jj][0], d1 = x1 - sx[jj][1], d2 = x2 - sx[jj][2];
-                                const T r2 = d0 * d0 + d1 * d1 + d2 * d2;
-                                if (r2 > T(0)) near += kernel_of_r2(kind, cc, r2) * sx[jj][3];
-                            }
-                        }
-                    }
+        for (int cb = 0; cb < nsrc; cb += kP2PChunk) {
+            __syncthreads();
+            const int cn = min(kP2PChunk, nsrc - cb);
+            for (int u = threadIdx.x; u < cn; u += kP2PThreads) {
+                const int g = cb + u;
+                int k = 0;
+                while (nb_pre[k + 1] <= g) ++k;
+                const int ps = perm[nb_start[k] + (g - nb_pre[k])];
+                sx[u][0] = xyz[3 * ps];
+                sx[u][1] = xyz[3 * ps + 1];
+                sx[u][2] = xyz[3 * ps + 2];
+                sx[u][3] = q[ps];
+            }
+            __syncthreads();
+            if (live) {
+#pragma unroll 4
+                for (int jj = 0; jj < cn; ++jj) {
+                    const T d0 = x0 - sx[jj][0], d1 = x1 - sx[jj][1], d2 = x2 - sx[jj][2];
+                    const T r2 = d0 * d0 + d1 * d1 + d2 * d2;
+                    if (r2 > T(0)) near += kernel_of_r2(kind, cc, r2) * sx[jj][3];
                 }
+            }
+        }
         if (live) phi[p] = f + near;
     }
 }
@@ -516,7 +549,7 @@ m2l_status fmm_eval(const m2l_fmm *f, const T *xyz, const T *q, T *phi, int prec
         M2L_LAUNCH_CHECK("l2l_kernel");
     }
     if (V[leaf].ncells > 0) {
-        l2p_p2p_kernel<T><<<V[leaf].ncells, kFmmThreads, 0, s>>>(
+        l2p_p2p_kernel<T><<<V[leaf].ncells, kP2PThreads, 0, s>>>(
             ell, f->kind, f->c, V[leaf].ncells, V[leaf].ijk.as<int32_t>(), V[leaf].side, f->start.as<int32_t>(),
             f->perm.as<int32_t>(), xyz, q, f->lo, wl, f->xi.as<T>(), f->inv_den.as<T>(), V[leaf].F.as<T>(), phi);
         M2L_LAUNCH_CHECK("l2p_p2p_kernel");
