@@ -257,9 +257,9 @@ l2l_kernel(int ell, int ncells, const int32_t *__restrict__ ijk, int parent_side
 // restricted to them, exact coincidences skipped): one block per leaf, one thread
 // per target particle; the sources of all neighbours, concatenated, are staged in
 // shared memory in chunks.  Potentials are written in the particles' input order.
-template <typename T>
+template <typename T, int KIND>
 __global__ void __launch_bounds__(kP2PThreads)
-l2p_p2p_kernel(int ell, int kind, double c, int ncells, const int32_t *__restrict__ ijk, int side,
+l2p_p2p_kernel(int ell, double c, int ncells, const int32_t *__restrict__ ijk, int side,
                const int32_t *__restrict__ start, const int32_t *__restrict__ perm, const T *__restrict__ xyz,
                const T *__restrict__ q, double lo, double w, const T *__restrict__ xi, const T *__restrict__ inv_den,
                const T *__restrict__ F, T *__restrict__ phi)
@@ -339,7 +339,9 @@ l2p_p2p_kernel(int ell, int kind, double c, int ncells, const int32_t *__restric
                 for (int jj = 0; jj < cn; ++jj) {
                     const T d0 = x0 - sx[jj][0], d1 = x1 - sx[jj][1], d2 = x2 - sx[jj][2];
                     const T r2 = d0 * d0 + d1 * d1 + d2 * d2;
-                    if (r2 > T(0)) near += kernel_of_r2(kind, cc, r2) * sx[jj][3];
+                    // exact coincidences (the target itself) contribute nothing
+                    const T k = kernel_of_r2(KIND, cc, r2 > T(0) ? r2 : T(1));
+                    near += (r2 > T(0) ? k : T(0)) * sx[jj][3];
                 }
             }
         }
@@ -549,9 +551,12 @@ m2l_status fmm_eval(const m2l_fmm *f, const T *xyz, const T *q, T *phi, int prec
         M2L_LAUNCH_CHECK("l2l_kernel");
     }
     if (V[leaf].ncells > 0) {
-        l2p_p2p_kernel<T><<<V[leaf].ncells, kP2PThreads, 0, s>>>(
-            ell, f->kind, f->c, V[leaf].ncells, V[leaf].ijk.as<int32_t>(), V[leaf].side, f->start.as<int32_t>(),
-            f->perm.as<int32_t>(), xyz, q, f->lo, wl, f->xi.as<T>(), f->inv_den.as<T>(), V[leaf].F.as<T>(), phi);
+        auto kern = f->kind == M2L_K_INV_R ? l2p_p2p_kernel<T, M2L_K_INV_R>
+                    : f->kind == M2L_K_INV_R4 ? l2p_p2p_kernel<T, M2L_K_INV_R4>
+                                               : l2p_p2p_kernel<T, M2L_K_INV_SQRT_R2C2>;
+        kern<<<V[leaf].ncells, kP2PThreads, 0, s>>>(ell, f->c, V[leaf].ncells, V[leaf].ijk.as<int32_t>(), V[leaf].side,
+                                                    f->start.as<int32_t>(), f->perm.as<int32_t>(), xyz, q, f->lo, wl,
+                                                    f->xi.as<T>(), f->inv_den.as<T>(), V[leaf].F.as<T>(), phi);
         M2L_LAUNCH_CHECK("l2p_p2p_kernel");
     }
     return M2L_OK;
