@@ -56,7 +56,7 @@ __device__ __forceinline__ float kernel_of_r2<float>(int kind, float c, float r2
 }
 
 constexpr int kP2PThreads = 64;     // targets per pass of a near-field block
-constexpr int kP2PChunk = 1024;     // sources staged per chunk
+constexpr int kP2PChunk = 512;      // sources staged per chunk
 
 // Leaf cell of every particle (binned in double, as the cells are half-open
 // with the top face clamped) and the particle count per dense leaf cell.
@@ -298,28 +298,36 @@ l2p_p2p_kernel(int ell, double c, int ncells, const int32_t *__restrict__ ijk, i
     const T ctr[3] = {T(lo + w * (ci + 0.5)), T(lo + w * (cj + 0.5)), T(lo + w * (ck + 0.5))};
     const T half = T(0.5 * w);
     const T cc = T(c);
-    for (int tb = j0; tb < j1; tb += kP2PThreads) {
-        const int it = tb + threadIdx.x;
-        const bool live = it < j1;
-        const int p = live ? perm[it] : 0;
-        const T x0 = live ? xyz[3 * p] : T(0), x1 = live ? xyz[3 * p + 1] : T(0), x2 = live ? xyz[3 * p + 2] : T(0);
-        T f = T(0);
-        if (live) {
-            T L0[8], L1[8], L2[8];
-            lagrange(ell, (x0 - ctr[0]) / half, xi, inv_den, L0);
-            lagrange(ell, (x1 - ctr[1]) / half, xi, inv_den, L1);
-            lagrange(ell, (x2 - ctr[2]) / half, xi, inv_den, L2);
-            for (int a2 = 0; a2 < ell; ++a2) {
-                T s1 = T(0);
-                for (int a1 = 0; a1 < ell; ++a1) {
-                    T s0 = T(0);
-                    for (int a0 = 0; a0 < ell; ++a0) s0 += L0[a0] * sF[a0 + ell * (a1 + ell * a2)];
-                    s1 += L1[a1] * s0;
+    // two targets per thread and pass (up to 2 kP2PThreads per leaf in one sweep of the sources)
+    for (int tb = j0; tb < j1; tb += 2 * kP2PThreads) {
+        int p[2];
+        bool live[2];
+        T x[2][3], f[2], near[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int it = tb + r * kP2PThreads + threadIdx.x;
+            live[r] = it < j1;
+            p[r] = live[r] ? perm[it] : 0;
+            for (int d = 0; d < 3; ++d) x[r][d] = live[r] ? xyz[3 * p[r] + d] : T(0);
+            f[r] = T(0);
+            near[r] = T(0);
+            if (live[r]) {
+                T L0[8], L1[8], L2[8];
+                lagrange(ell, (x[r][0] - ctr[0]) / half, xi, inv_den, L0);
+                lagrange(ell, (x[r][1] - ctr[1]) / half, xi, inv_den, L1);
+                lagrange(ell, (x[r][2] - ctr[2]) / half, xi, inv_den, L2);
+                for (int a2 = 0; a2 < ell; ++a2) {
+                    T s1 = T(0);
+                    for (int a1 = 0; a1 < ell; ++a1) {
+                        T s0 = T(0);
+                        for (int a0 = 0; a0 < ell; ++a0) s0 += L0[a0] * sF[a0 + ell * (a1 + ell * a2)];
+                        s1 += L1[a1] * s0;
+                    }
+                    f[r] += L2[a2] * s1;
                 }
-                f += L2[a2] * s1;
             }
         }
-        T near = T(0);
+        const bool any1 = tb + kP2PThreads < j1;   // block-uniform: a second target per thread exists
         for (int cb = 0; cb < nsrc; cb += kP2PChunk) {
             __syncthreads();
             const int cn = min(kP2PChunk, nsrc - cb);
@@ -334,18 +342,34 @@ l2p_p2p_kernel(int ell, double c, int ncells, const int32_t *__restrict__ ijk, i
                 sx[u][3] = q[ps];
             }
             __syncthreads();
-            if (live) {
+            if (any1) {
+                if (live[0]) {
+#pragma unroll 4
+                    for (int jj = 0; jj < cn; ++jj) {
+                        const T sq = sx[jj][3];
+#pragma unroll
+                        for (int r = 0; r < 2; ++r) {
+                            const T d0 = x[r][0] - sx[jj][0], d1 = x[r][1] - sx[jj][1], d2 = x[r][2] - sx[jj][2];
+                            const T r2 = d0 * d0 + d1 * d1 + d2 * d2;
+                            // exact coincidences (the target itself) contribute nothing
+                            const T k = kernel_of_r2(KIND, cc, r2 > T(0) ? r2 : T(1));
+                            near[r] += (r2 > T(0) ? k : T(0)) * sq;
+                        }
+                    }
+                }
+            } else if (live[0]) {
 #pragma unroll 4
                 for (int jj = 0; jj < cn; ++jj) {
-                    const T d0 = x0 - sx[jj][0], d1 = x1 - sx[jj][1], d2 = x2 - sx[jj][2];
+                    const T d0 = x[0][0] - sx[jj][0], d1 = x[0][1] - sx[jj][1], d2 = x[0][2] - sx[jj][2];
                     const T r2 = d0 * d0 + d1 * d1 + d2 * d2;
-                    // exact coincidences (the target itself) contribute nothing
                     const T k = kernel_of_r2(KIND, cc, r2 > T(0) ? r2 : T(1));
-                    near += (r2 > T(0) ? k : T(0)) * sx[jj][3];
+                    near[0] += (r2 > T(0) ? k : T(0)) * sx[jj][3];
                 }
             }
         }
-        if (live) phi[p] = f + near;
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+            if (live[r]) phi[p[r]] = f[r] + near[r];
     }
 }
 
