@@ -439,6 +439,28 @@ def roofline(precision, achieved_tflops, peaks, src_kind):
             "flop_convention": "algorithmic 2*ell^6 per interaction, level-5 launch"}
 
 
+def precompute_times(m2l, device, reps=3):
+    """Wall time of m2l_precompute (step a1: the 16 operators, tables and, with
+    eps > 0, the per-operator truncated SVD) for the bench's order and for the
+    mixed-precision workload's ell = 7, 1/r^4, eps = 1e-7."""
+    import torch
+    out = {}
+    for name, kind, ell, eps in (("full_ell5_inv_r", m2l.M2L_K_INV_R, ELL, 0.0),
+                                 ("svd_ell7_inv_r4_eps1e-7", m2l.M2L_K_INV_R4, 7, 1e-7)):
+        m2l.m2l_precompute(kind, ell, eps)   # first call: module load, workspace
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize(device)
+            t0 = time.perf_counter()
+            ops = m2l.m2l_precompute(kind, ell, eps)
+            torch.cuda.synchronize(device)
+            ts.append(1e3 * (time.perf_counter() - t0))
+            del ops
+        out[name] = round(statistics.median(ts), 3)
+    out["unit"] = "ms (synchronous call, host wall time)"
+    return out
+
+
 def fmm_matvec(m2l, device, precision, reps=5):
     """The whole bbFMM matvec of the workload's particles on the GPU
     (m2l_fmm_evaluate: P2M, M2M, M2L at levels 2-5, L2L, L2P and near field);
@@ -544,6 +566,7 @@ def run_ours(args):
             except m2l.M2LError as e:
                 extra[p] = {"unavailable": str(e)}
     fmm = fmm_matvec(m2l, device, prec) if (rank == 0 and not args.quick and prec != "fp64") else None
+    pre = precompute_times(m2l, device) if (rank == 0 and not args.quick) else None
     cpu = None
     if rank == 0 and world == 1 and not args.quick:
         cpu, ref_loc = cpu_oracle_sample(with_locals=True)
@@ -566,6 +589,7 @@ def run_ours(args):
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches,
                 "fmm_matvec": fmm,
+                "precompute": pre,
                 "clocks": clk,
                 "precisions": extra}
         print(json.dumps(line), flush=True)
