@@ -20,7 +20,8 @@ What it computes, each function citing its source:
 * The symmetry maps of Sec. 4.2.1: axial and diagonal multi-index
   permutations (Eqs. (26)-(27)), T_sym (Eqs. (23)-(24)) and p(t).
 * Cell-by-cell M2L f_X += K_t w_Y (Eq. (7)) and its adjoint, in plain C loops.
-* Truncated SVD per operator (Eq. (20)).
+* Truncated SVD per operator (Eq. (20)); the single low-rank approximation
+  SA of all operators and its recompression SArcmp (Sec. 4.1).
 * P2M/M2M (Eq. (6)), L2L/L2P (Eq. (8)), P2P and the direct sum (Eq. (1)).
 
 Readings of the paper taken where it is silent or garbled (each stated where
@@ -353,6 +354,79 @@ def lowrank_operator_table(ops: np.ndarray, eps: float):
         out[s] = U @ V.T
         ranks[s] = r
     return out, ranks
+
+
+# --------------------------------------------------------------------------
+# single low-rank approximation (SA) and its recompression (SArcmp), Sec. 4.1
+# --------------------------------------------------------------------------
+def sa_factors(ops: np.ndarray, eps: float):
+    """SA of Sec. 4.1, Eqs. (17)-(18), for the 316 operators of a level.
+
+    The operators of T are joined as a row K_row = [K_t1, ..., K_t316] and as a
+    column K_col = [K_t1; ...; K_t316] (T in the order of transfer_vectors());
+    K_row ~ U Sigma V^*, K_col ~ A Gamma B^* by truncated SVDs.  The paper gives
+    one rank r for both; it is read here as the larger of the two truncation
+    ranks at accuracy eps (same spectral criterion as Eq. (20)).  Then
+    K_t ~ U C_t B^* with C_t = U^* K_t B.
+
+    Returns dict: U [n3, r], B [n3, r], C [343, r, r] at the t-slots (zeros
+    elsewhere), r, the singular values of K_row and K_col, and, for the pins,
+    Sigma V_t^* B and U^* A_t Gamma (the paper's two other forms of C_t).
+    """
+    ts = transfer_vectors()
+    Ks = [ops[t_slot(t)] for t in ts]
+    n3 = Ks[0].shape[0]
+    Urow, s_row, Vh_row = np.linalg.svd(np.concatenate(Ks, axis=1), full_matrices=False)
+    Acol, s_col, Bh_col = np.linalg.svd(np.concatenate(Ks, axis=0), full_matrices=False)
+    r = max(truncation_rank(s_row, eps), truncation_rank(s_col, eps))
+    U, B = Urow[:, :r], Bh_col[:r, :].T
+    C = np.zeros((343, r, r))
+    C_sv = np.zeros((343, r, r))
+    C_ag = np.zeros((343, r, r))
+    for i, t in enumerate(ts):
+        sl = t_slot(t)
+        C[sl] = U.T @ Ks[i] @ B
+        C_sv[sl] = (s_row[:r, None] * Vh_row[:r, i * n3:(i + 1) * n3]) @ B
+        C_ag[sl] = U.T @ (Acol[i * n3:(i + 1) * n3, :r] * s_col[None, :r])
+    return {"U": U, "B": B, "C": C, "r": r, "s_row": s_row, "s_col": s_col, "C_sigma_v": C_sv,
+            "C_a_gamma": C_ag}
+
+
+def sa_recompress(C: np.ndarray, r: int, eps: float):
+    """SArcmp, Eq. (19) of Sec. 4.1.1: each C_t ~ Ubar_t Vbar_t^* with rank
+    r_t (same criterion at accuracy eps, relative to C_t's largest singular
+    value), kept only when r_t < r / 2; otherwise C_t stays as it is.
+
+    Returns (table [343, r, r] of the represented C_t, ranks [343]: r_t, or r
+    where C_t is kept whole, 0 at unused slots).
+    """
+    out = np.zeros_like(C)
+    ranks = np.zeros(343, dtype=np.int64)
+    for t in transfer_vectors():
+        sl = t_slot(t)
+        u, sv, vh = np.linalg.svd(C[sl])
+        rt = truncation_rank(sv, eps)
+        if 2 * rt < r:
+            out[sl] = (u[:, :rt] * sv[None, :rt]) @ vh[:rt, :]
+            ranks[sl] = rt
+        else:
+            out[sl] = C[sl]
+            ranks[sl] = r
+    return out, ranks
+
+
+def sa_operator_table(ops: np.ndarray, eps: float, recompress: bool = False):
+    """The SA (or SArcmp) operators U C_t B^* at the t-slots, for m2l_apply.
+
+    Returns (table [343, n3, n3], sa dict, recompression ranks or None).
+    """
+    sa = sa_factors(ops, eps)
+    C, ranks = (sa_recompress(sa["C"], sa["r"], eps) if recompress else (sa["C"], None))
+    out = np.zeros_like(ops)
+    for t in transfer_vectors():
+        sl = t_slot(t)
+        out[sl] = sa["U"] @ C[sl] @ sa["B"].T
+    return out, sa, ranks
 
 
 # --------------------------------------------------------------------------

@@ -406,3 +406,69 @@ def test_apply_rejects_near_field_pair():
 def test_rel_err_definition():
     assert o.rel_l2([1.0, 2.0], [1.0, 2.0]) == 0.0
     assert abs(o.rel_l2([0.0, 0.0], [3.0, 4.0]) - 1.0) < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# SA / SArcmp (Sec. 4.1)
+# ---------------------------------------------------------------------------
+def _ops_l4():
+    return o.operator_table(4, 0, 0.0, 3)
+
+
+def test_sa_three_forms_of_c_agree():
+    """Eq. (18): C_t = U^* K_t B = Sigma V_t^* B = U^* A_t Gamma (exact even
+    after truncation: the residuals are orthogonal to U and to B)."""
+    sa = o.sa_factors(_ops_l4(), 1e-6)
+    assert 0 < sa["r"] < 64
+    for t in o.transfer_vectors()[::7]:
+        sl = o.t_slot(t)
+        c = sa["C"][sl]
+        scale = np.abs(c).max()
+        assert np.abs(sa["C_sigma_v"][sl] - c).max() < 1e-12 * scale
+        assert np.abs(sa["C_a_gamma"][sl] - c).max() < 1e-12 * scale
+
+
+def test_sa_error_bound_and_exact_limit():
+    """||K_t - U C_t B^*||_2 <= s_{r+1}(K_row) + s_{r+1}(K_col) for every t; with
+    eps = 0 the representation is exact."""
+    ops = _ops_l4()
+    for eps in (1e-3, 1e-6):
+        table, sa, _ = o.sa_operator_table(ops, eps)
+        r = sa["r"]
+        bound = sa["s_row"][r] + sa["s_col"][r] if r < len(sa["s_row"]) else 0.0
+        for t in o.transfer_vectors():
+            sl = o.t_slot(t)
+            err = np.linalg.norm(ops[sl] - table[sl], 2)
+            assert err <= bound * (1 + 1e-8) + 1e-13 * np.linalg.norm(ops[sl], 2), (eps, t, err, bound)
+    table, sa, _ = o.sa_operator_table(ops, 0.0)
+    assert sa["r"] == 64
+    for t in o.transfer_vectors()[::11]:
+        sl = o.t_slot(t)
+        assert np.abs(table[sl] - ops[sl]).max() < 1e-12 * np.abs(ops[sl]).max()
+
+
+def test_sa_rank_decreases_with_eps():
+    ops = _ops_l4()
+    ranks = [o.sa_factors(ops, e)["r"] for e in (1e-9, 1e-6, 1e-3, 1e-1)]
+    assert all(a >= b for a, b in zip(ranks, ranks[1:])) and ranks[0] > ranks[-1]
+
+
+def test_sarcmp_recompression():
+    """Eq. (19): a recompressed C_t has rank r_t < r/2 and differs from C_t by
+    its (r_t+1)-th singular value (Eckart-Young); the others are kept whole."""
+    ops = _ops_l4()
+    sa = o.sa_factors(ops, 1e-4)
+    C2, ranks = o.sa_recompress(sa["C"], sa["r"], 1e-4)
+    n_re = 0
+    for t in o.transfer_vectors():
+        sl = o.t_slot(t)
+        sv = np.linalg.svd(sa["C"][sl], compute_uv=False)
+        if ranks[sl] < sa["r"]:
+            n_re += 1
+            assert 2 * ranks[sl] < sa["r"]
+            err = np.linalg.norm(C2[sl] - sa["C"][sl], 2)
+            assert abs(err - sv[ranks[sl]]) <= 1e-10 * sv[0]
+            assert sv[ranks[sl]] <= 1e-4 * sv[0]
+        else:
+            assert np.array_equal(C2[sl], sa["C"][sl])
+    assert n_re > 0
