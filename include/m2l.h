@@ -284,6 +284,49 @@ m2l_status m2l_fmm_info(const m2l_fmm *fmm, int *leaf_level, int64_t *ncells9, i
 void m2l_fmm_free(m2l_fmm *fmm);
 
 /* ---------------------------------------------------------------------
+ * SA and SArcmp (Sec. 4.1, Eqs. (17)-(19)): the alternative that compresses
+ * all 316 operators of a level with ONE pair of bases instead of using their
+ * symmetries.  The operators are joined as K_row = [K_t1 ... K_t316] and
+ * K_col = [K_t1; ...; K_t316]; truncated SVDs K_row ~ U S V^T and
+ * K_col ~ A G B^T give K_t ~ U C_t B^T with the r x r cores C_t = U^T K_t B
+ * (Eq. (18)).  r is the larger of the two truncation ranks at relative
+ * accuracy eps (singular values above eps times the largest; eps = 0 keeps
+ * all n3 = ell^3 of them).  SArcmp (recompress != 0, Eq. (19)) replaces a
+ * core by its truncated SVD X_t Y_t^T of rank r_t (same criterion, relative
+ * to C_t's largest singular value) when 2 r_t < r; otherwise C_t is kept.
+ *
+ * m2l_sa_create: builds the factors of the operators in ops (full rank, any
+ *   eps of ops; only ops' 16 unique operators and their symmetries are
+ *   read) in FP64 on the device with cuSOLVER; synchronous; allocates what
+ *   it keeps.  eps in [0, 1).  r <= 128 (larger: M2L_EUNSUPPORTED).
+ * m2l_sa_info: r, the number of recompressed cores and (host [343], may be
+ *   NULL) r_t per t-slot (t + 3) . (1, 7, 49), 0 where C_t is kept whole or
+ *   the slot is not a far-field transfer vector.
+ * m2l_sa_copy_factors: host copies (FP64) of U^T [r][n3], B [n3][r], and the
+ *   per-slot X [343][r][r] and Y [343][r][r]: X holds C_t where r_t = 0,
+ *   else X_t in its first r_t columns with Y_t in Y's; NULL skips one.
+ *   Synchronous.
+ * m2l_sa_apply_level: locals[X] += scale U C_t B^T multipoles[Y] over the
+ *   level's list, computed as compress (w^ = B^T w for every source cell),
+ *   cores per transfer vector (f^[X] += C_t w^[Y]), decompress
+ *   (F += scale U f^); scale as m2l_apply_level.  precision M2L_FP64 (double
+ *   vectors) or M2L_FP32 (float multipoles; locals float, or double with
+ *   locals_fp64 != 0).  Stream-ordered; allocates its workspace on first
+ *   use or growth; list errors as m2l_apply_level (skipped entries, reported
+ *   by m2l_sync_status on sa's ops).  Work on one m2l_sa object must be
+ *   ordered on one stream.
+ * Errors: M2L_EINVAL (null or bad arguments), M2L_EUNSUPPORTED (rank,
+ *   precision), M2L_ECUDA / M2L_ENOMEM. */
+typedef struct m2l_sa m2l_sa;
+m2l_status m2l_sa_create(const m2l_ops *ops, double eps, int recompress, void *stream, m2l_sa **out);
+m2l_status m2l_sa_info(const m2l_sa *sa, int *rank, int *n_recompressed, int32_t *host_rt343);
+m2l_status m2l_sa_copy_factors(const m2l_sa *sa, double *host_Ut, double *host_B, double *host_X,
+                               double *host_Y);
+m2l_status m2l_sa_apply_level(const m2l_sa *sa, const m2l_level *level, const void *multipoles, void *locals,
+                              int precision, int locals_fp64, void *stream);
+void m2l_sa_free(m2l_sa *sa);
+
+/* ---------------------------------------------------------------------
  * Interaction lists (Sec. 3.2, Alg. 1 for asymptotically smooth kernels):
  * Y is in the list of X when their parents are neighbours,
  * |floor(X/2) - floor(Y/2)|_inf <= 1, and |X - Y|_inf >= 2.  Sources of a

@@ -79,6 +79,10 @@ def lib():
             "m2l_batch_info": [P, P, P, P],
             "m2l_sync_status": [P, P],
             "m2l_ops_set_debug": [P, I],
+            "m2l_sa_create": [P, D, I, P, ctypes.POINTER(P)],
+            "m2l_sa_info": [P, P, P, P],
+            "m2l_sa_copy_factors": [P, P, P, P, P],
+            "m2l_sa_apply_level": [P, ctypes.POINTER(m2l_level), P, P, I, I, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -92,6 +96,8 @@ def lib():
         L.m2l_batch_free.restype = None
         L.m2l_fmm_free.argtypes = [P]
         L.m2l_fmm_free.restype = None
+        L.m2l_sa_free.argtypes = [P]
+        L.m2l_sa_free.restype = None
         L.m2l_last_error.argtypes = []
         L.m2l_last_error.restype = ctypes.c_char_p
         L.m2l_launch_count.argtypes = []
@@ -468,3 +474,52 @@ def m2l_fmm_query(fmm: FMM, level: int):
     _check("m2l_fmm_query", lib().m2l_fmm_query(fmm.handle, int(level), ijk.ctypes.data, W.ctypes.data,
                                                 F.ctypes.data))
     return ijk[:n], W[:n], F[:n]
+
+
+class SA:
+    """SA / SArcmp factors of one operator set (Sec. 4.1), built by m2l_sa_create."""
+
+    def __init__(self, handle, ops, eps, recompress):
+        self.handle, self.ops, self.eps, self.recompress = handle, ops, eps, recompress
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.m2l_sa_free(h)
+
+
+def m2l_sa_create(ops: Ops, eps, recompress=False, stream=None) -> SA:
+    h = ctypes.c_void_p()
+    _check("m2l_sa_create", lib().m2l_sa_create(ops.handle, float(eps), int(bool(recompress)), _stream_ptr(stream),
+                                                ctypes.byref(h)))
+    return SA(h, ops, float(eps), bool(recompress))
+
+
+def m2l_sa_info(sa: SA):
+    """(rank r, number of recompressed cores, r_t per t-slot [343] (0: C_t kept whole))."""
+    r, nrc = ctypes.c_int(), ctypes.c_int()
+    rt = np.zeros(343, dtype=np.int32)
+    _check("m2l_sa_info", lib().m2l_sa_info(sa.handle, ctypes.byref(r), ctypes.byref(nrc), rt.ctypes.data))
+    return r.value, nrc.value, rt
+
+
+def m2l_sa_copy_factors(sa: SA):
+    """Host FP64 (U [n3, r], B [n3, r], X [343, r, r], Y [343, r, r])."""
+    r, _, _ = m2l_sa_info(sa)
+    n3 = sa.ops.n3
+    Ut = np.zeros((r, n3))
+    B = np.zeros((n3, r))
+    X = np.zeros((343, r, r))
+    Y = np.zeros((343, r, r))
+    _check("m2l_sa_copy_factors", lib().m2l_sa_copy_factors(sa.handle, Ut.ctypes.data, B.ctypes.data,
+                                                            X.ctypes.data, Y.ctypes.data))
+    return Ut.T.copy(), B, X, Y
+
+
+def m2l_sa_apply_level(sa: SA, level: Level, multipoles, locals_, precision="fp32", locals_fp64=False,
+                       stream=None):
+    p, tin, tout = _vec_dtypes(precision, locals_fp64)
+    _check_shapes(sa.ops, multipoles, locals_, level.struct.ncells_src, level.struct.ncells_tgt)
+    _check("m2l_sa_apply_level", lib().m2l_sa_apply_level(
+        sa.handle, ctypes.byref(level.struct), _dev_ptr(multipoles, tin, "multipoles"),
+        _dev_ptr(locals_, tout, "locals"), p, int(bool(locals_fp64)), _stream_ptr(stream)))

@@ -63,6 +63,11 @@ def test_null_handles_rejected(lib):
     assert lib.m2l_fmm_create(None, 0, None, 0, 3, -1.0, 2.0, None, None) == m2l.M2L_EINVAL
     assert lib.m2l_fmm_evaluate(None, None, None, None, 1, None) == m2l.M2L_EINVAL
     assert lib.m2l_fmm_info(None, None, None, None) == m2l.M2L_EINVAL
+    assert lib.m2l_sa_create(None, 1e-5, 0, None, None) == m2l.M2L_EINVAL
+    assert lib.m2l_sa_info(None, None, None, None) == m2l.M2L_EINVAL
+    assert lib.m2l_sa_copy_factors(None, None, None, None, None) == m2l.M2L_EINVAL
+    assert lib.m2l_sa_apply_level(None, None, None, None, 1, 0, None) == m2l.M2L_EINVAL
+    lib.m2l_sa_free(None)
     lib.m2l_fmm_free(None)
     lib.m2l_ops_free(None)
     lib.m2l_plan_free(None)
