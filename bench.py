@@ -461,6 +461,57 @@ def precompute_times(m2l, device, reps=3):
     return out
 
 
+def variants_compare(m2l, device, wl, flush, eps=1e-5, reps=5):
+    """The level-5 apply of the workload in the paper's other variants at one
+    accuracy eps (Sec. 4): SA and SArcmp (one basis for all 316 operators,
+    Eqs. (17)-(19)) and the symmetry-blocked path on per-operator truncated
+    SVDs (Eq. (20) with Sec. 4.2), all FP32, each with its own bucketing of the
+    list; error against the FP64 full-rank result of the same level."""
+    import torch
+    lv = wl.levels[5]
+    n3 = ELL ** 3
+    mp64 = wl.mp[5].double()
+    ref = torch.zeros(lv.struct.ncells_tgt, n3, dtype=torch.float64, device=device)
+    m2l.m2l_apply_level(wl.ops, lv, mp64, ref, "fp64")
+    mp32 = wl.mp[5].float().contiguous()
+    out = {"eps": eps, "level": 5, "interactions": lv.nnz, "precision": "fp32"}
+
+    def run(name, fn, info):
+        loc = torch.zeros(lv.struct.ncells_tgt, n3, dtype=torch.float32, device=device)
+        fn(loc)
+        torch.cuda.synchronize(device)
+        err = float(torch.linalg.norm(loc.double() - ref) / torch.linalg.norm(ref))
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn(loc)
+            e1.record()
+            torch.cuda.synchronize(device)
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        out[name] = dict(info, ms=ms, interactions_per_s=lv.nnz / (ms / 1e3), rel_l2_vs_fp64_full=err)
+
+    for rc in (False, True):
+        t0 = time.perf_counter()
+        sa = m2l.m2l_sa_create(wl.ops, eps, rc)
+        setup = 1e3 * (time.perf_counter() - t0)
+        r, nrc, _ = m2l.m2l_sa_info(sa)
+        run("sarcmp" if rc else "sa", lambda loc, sa=sa: m2l.m2l_sa_apply_level(sa, lv, mp32, loc, "fp32"),
+            {"rank": r, "recompressed_cores": nrc, "setup_ms": round(setup, 1)})
+        del sa
+    t0 = time.perf_counter()
+    ops_lr = m2l.m2l_precompute(m2l.M2L_K_INV_R, ELL, eps)
+    setup = 1e3 * (time.perf_counter() - t0)
+    ranks = m2l.m2l_ops_query(ops_lr)[0]
+    run("blocked_lowrank", lambda loc: m2l.m2l_apply_level(ops_lr, lv, mp32, loc, "fp32"),
+        {"ranks_min_max": [int(ranks.min()), int(ranks.max())], "setup_ms": round(setup, 1)})
+    m2l.m2l_sync_status(wl.ops)
+    m2l.m2l_sync_status(ops_lr)
+    return out
+
+
 def fmm_matvec(m2l, device, precision, reps=5):
     """The whole bbFMM matvec of the workload's particles on the GPU
     (m2l_fmm_evaluate: P2M, M2M, M2L at levels 2-5, L2L, L2P and near field);
@@ -567,6 +618,7 @@ def run_ours(args):
                 extra[p] = {"unavailable": str(e)}
     fmm = fmm_matvec(m2l, device, prec) if (rank == 0 and not args.quick and prec != "fp64") else None
     pre = precompute_times(m2l, device) if (rank == 0 and not args.quick) else None
+    variants = variants_compare(m2l, device, wl, flush) if (rank == 0 and not args.quick) else None
     cpu = None
     if rank == 0 and world == 1 and not args.quick:
         cpu, ref_loc = cpu_oracle_sample(with_locals=True)
@@ -590,6 +642,7 @@ def run_ours(args):
                 "gpu_launches": launches,
                 "fmm_matvec": fmm,
                 "precompute": pre,
+                "variants": variants,
                 "clocks": clk,
                 "precisions": extra}
         print(json.dumps(line), flush=True)
