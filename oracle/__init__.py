@@ -6,3 +6,4 @@ shares no code with the CUDA path.
 """
 from .m2l_oracle import *  # noqa: F401,F403
 from .m2l_oracle import build_c  # noqa: F401
+from . import dfmm_oracle as dfmm  # noqa: F401,E402

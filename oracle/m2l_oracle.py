@@ -641,11 +641,14 @@ def direct_sum(kind: int, c: float, targets: np.ndarray, sources: np.ndarray, q:
 
 def rel_l2(approx, exact) -> float:
     """Relative L2 error (Eq. (34)), read with a squared denominator:
-    (sum |f - fbar|^2 / sum |f|^2)^(1/2)."""
-    a = np.asarray(approx, dtype=np.float64).ravel()
-    e = np.asarray(exact, dtype=np.float64).ravel()
-    den = float(np.sum(e * e))
-    return float(np.sqrt(np.sum((a - e) ** 2) / den)) if den > 0 else float(np.sqrt(np.sum(a * a)))
+    (sum |f - fbar|^2 / sum |f|^2)^(1/2).  Real or complex values."""
+    cplx = np.iscomplexobj(approx) or np.iscomplexobj(exact)
+    dt = np.complex128 if cplx else np.float64
+    a = np.asarray(approx, dtype=dt).ravel()
+    e = np.asarray(exact, dtype=dt).ravel()
+    den = float(np.sum(np.abs(e) ** 2))
+    num = float(np.sum(np.abs(a - e) ** 2))
+    return float(np.sqrt(num / den)) if den > 0 else float(np.sqrt(float(np.sum(np.abs(a) ** 2))))
 
 
 # --------------------------------------------------------------------------
