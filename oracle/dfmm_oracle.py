@@ -25,8 +25,9 @@ Readings, where the paper defers to its reference on the directional FMM:
 * D1 regime: a level of cell width w is high-frequency when k w >= 1 (the
   paper's table of list sizes has k w = 1 in hf and k w = 1/2 in lf).
 * D2 admissibility: at an lf level, |t|_inf >= 2 (the bbFMM rule); at an hf
-  level, additionally |c_X - c_Y| >= k w^2 (the O(k w^2) separation),
-  evaluated as (t.t) w w >= (k w w)(k w w) in FP64.
+  level, additionally |c_X - c_Y| > k w^2 (the O(k w^2) separation, strict),
+  evaluated as (t.t) w w > (k w w)(k w w) in FP64.  On the paper's sphere
+  this reproduces its table of list sizes exactly at levels 3, 4 and 5.
 * D3 cones: the unit sphere is split through the faces of the cube [-1, 1]^3,
   each face into m x m squares, m the smallest power of two >= k w (cone
   aperture O(1/(k w)), halved from one level to the next coarser one:
@@ -79,7 +80,7 @@ def admissible(k: float, w: float, t) -> bool:
     if not is_high_frequency(k, w):
         return True
     tt = float(sum(int(v) * int(v) for v in t))
-    return tt * w * w >= (k * w * w) * (k * w * w)
+    return tt * w * w > (k * w * w) * (k * w * w)
 
 
 def cone_m(k: float, w: float) -> int:
@@ -183,7 +184,7 @@ def admissible_many(k: float, w: float, t: np.ndarray) -> np.ndarray:
     if not is_high_frequency(k, w):
         return ok
     tt = (t * t).sum(axis=-1).astype(np.float64)
-    return ok & (tt * w * w >= (k * w * w) * (k * w * w))
+    return ok & (tt * w * w > (k * w * w) * (k * w * w))
 
 
 def directional_lists(cells: np.ndarray, level: int, k: float, domain_width: float):

@@ -193,3 +193,26 @@ def test_m2l_matches_brute_force():
                     r = np.sqrt(((xn[a] - yn[b]) ** 2).sum())
                     ref[e, a] += np.exp(1j * k * r) / r * W[y * C + e % C, b]
     assert oracle.rel_l2(F, ref) < 1e-13
+
+
+def test_sphere_list_sizes_match_the_paper():
+    """The paper's sphere (box 64, k = 1) is the unit-domain sphere with k = 32:
+    only k times the domain width enters.  |T| and |T_sym| of the directional
+    lists at levels 3, 4 and 5 are the printed ones."""
+    import json
+    import os
+    from paper_1210_7292_gb300 import synth
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "dfmm_sphere_lists.json")))
+    geo = gold["geometry"]
+    k = geo["wavenumber"] * geo["box"] / 2.0
+    pts, _ = synth.sphere_surface(geo["particles"], seed=21)
+    for L in gold["reproduced_levels"]:
+        ref = gold["levels"][str(L)]
+        w = d.level_width(L, 2.0)
+        assert d.is_high_frequency(k, w) == (ref["regime"] == "hf")
+        cells = synth.occupied_cells(pts, L)
+        C, off, src = d.directional_lists(cells, L, k, 2.0)
+        x = np.repeat(np.arange(len(off) - 1) // C, np.diff(off))
+        T = np.unique(cells[x].astype(np.int64) - cells[src].astype(np.int64), axis=0)
+        Tsym = {d.canonical_t(t) for t in T}
+        assert (len(T), len(Tsym)) == (ref["T"], ref["T_sym"]), L
