@@ -512,6 +512,74 @@ def variants_compare(m2l, device, wl, flush, eps=1e-5, reps=5):
     return out
 
 
+DFMM_PARTICLES = 168931   # the paper's sphere (Sec. 5)
+DFMM_K = 32.0             # k = 1 in its box of side 64, on the unit domain of side 2
+DFMM_LEVELS = (3, 4, 5, 6)
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+
+
+def dfmm_m2l(m2l, device, reps=5):
+    """The directional (Helmholtz) M2L of the paper's sphere at ell = 5 over its
+    high-frequency levels 3-6: lists and plans built once (set-up, timed apart),
+    then every level's complex M2L per pass, FP32 and FP64 (the FP32 error
+    against FP64 over all levels)."""
+    import torch
+
+    from paper_1210_7292_gb300 import synth
+    ell = ELL
+    n3 = ell ** 3
+    pts, _ = synth.sphere_surface(DFMM_PARTICLES, seed=21)
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    plans, vecs, per_level = {}, {}, {}
+    for L in DFMM_LEVELS:
+        ijk = torch.from_numpy(synth.occupied_cells(pts, L)).to(device)
+        C, off, src = m2l.m2l_dfmm_build_lists(L, DFMM_K, ijk)
+        lv = m2l.DLevel(2.0 / (1 << L), ijk, ijk, C, off, src, L)
+        plans[L] = m2l.m2l_dfmm_plan_create(ell, DFMM_K, lv)
+        tsym, _, _, nnz = m2l.m2l_dfmm_plan_info(plans[L])
+        g = torch.Generator(device=device).manual_seed(SEED + L)
+        n = ijk.shape[0] * C * n3
+        w = torch.complex(torch.randn(n, generator=g, device=device, dtype=torch.float64),
+                          torch.randn(n, generator=g, device=device, dtype=torch.float64))
+        vecs[L] = w
+        per_level[L] = {"cells": int(ijk.shape[0]), "cones": C, "interactions": int(nnz), "T_sym": int(len(tsym))}
+    setup_ms = 1e3 * (time.perf_counter() - t0)
+    total = sum(v["interactions"] for v in per_level.values())
+    flops = 8.0 * n3 * n3 * total
+    out = {"workload": "sphere, %d particles, k w = 8, 4, 2, 1 at levels 3-6, ell = %d" % (DFMM_PARTICLES, ell),
+           "levels": per_level, "interactions": total, "setup_ms": round(setup_ms, 1),
+           "flop_convention": "8 ell^6 real flops per complex interaction"}
+    res = {}
+    for prec, dt in (("fp64", torch.complex128), ("fp32", torch.complex64)):
+        W = {L: vecs[L].to(dt) for L in DFMM_LEVELS}
+        F = {L: torch.zeros_like(W[L]) for L in DFMM_LEVELS}
+
+        def one():
+            for L in DFMM_LEVELS:
+                m2l.m2l_dfmm_plan_apply(plans[L], W[L], F[L], prec)
+        one()
+        torch.cuda.synchronize(device)
+        res[prec] = {L: F[L].to(torch.complex128).clone() for L in DFMM_LEVELS}
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            one()
+            e1.record()
+            torch.cuda.synchronize(device)
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        out[prec] = {"ms": ms, "interactions_per_s": total / (ms / 1e3), "tflops": flops / (ms / 1e3) / 1e12}
+    num = sum(float(torch.linalg.norm(res["fp32"][L] - res["fp64"][L]) ** 2) for L in DFMM_LEVELS)
+    den = sum(float(torch.linalg.norm(res["fp64"][L]) ** 2) for L in DFMM_LEVELS)
+    out["fp32"]["rel_l2_vs_fp64"] = (num / den) ** 0.5
+    out["fp32"]["roofline"] = {"bound": "alu", "peak_tflops": round(FP32_ALU_TFLOPS, 1),
+                               "frac": out["fp32"]["tflops"] / FP32_ALU_TFLOPS,
+                               "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (derived)"}
+    return out
+
+
 def fmm_matvec(m2l, device, precision, reps=5):
     """The whole bbFMM matvec of the workload's particles on the GPU
     (m2l_fmm_evaluate: P2M, M2M, M2L at levels 2-5, L2L, L2P and near field);
@@ -619,6 +687,7 @@ def run_ours(args):
     fmm = fmm_matvec(m2l, device, prec) if (rank == 0 and not args.quick and prec != "fp64") else None
     pre = precompute_times(m2l, device) if (rank == 0 and not args.quick) else None
     variants = variants_compare(m2l, device, wl, flush) if (rank == 0 and not args.quick) else None
+    dfmm = dfmm_m2l(m2l, device) if (rank == 0 and not args.quick) else None
     cpu = None
     if rank == 0 and world == 1 and not args.quick:
         cpu, ref_loc = cpu_oracle_sample(with_locals=True)
@@ -643,6 +712,7 @@ def run_ours(args):
                 "fmm_matvec": fmm,
                 "precompute": pre,
                 "variants": variants,
+                "dfmm_m2l": dfmm,
                 "clocks": clk,
                 "precisions": extra}
         print(json.dumps(line), flush=True)

@@ -327,6 +327,77 @@ m2l_status m2l_sa_apply_level(const m2l_sa *sa, const m2l_level *level, const vo
 void m2l_sa_free(m2l_sa *sa);
 
 /* ---------------------------------------------------------------------
+ * Directional FMM (dFMM) M2L for the Helmholtz kernel (Sec. 2.1.2):
+ *   F^u_X += K_t W^u_Y,  (K_t)_{ab} = exp(i k r_ab) / r_ab,  r_ab = |xbar_a - ybar_b|
+ * (Eq. (13); the 4 pi of Eq. (33) dropped like for the other kernels).  The
+ * directional phases exp(+-i k u.x) belong to P2M and L2P (Eqs. (12), (14));
+ * the M2L operator is the plain kernel, identical for every cone, and the 48
+ * symmetries of Sec. 4.2.1 apply to any transfer vector.  Each cell of a
+ * level holds one expansion per cone: multipoles and locals are complex,
+ * interleaved (re, im), [ncells][n_cones][ell^3] (complex double for
+ * M2L_FP64, complex float for M2L_FP32).
+ *
+ * Readings (the paper defers these to its reference on the dFMM):
+ *  - a level of cell width w is high-frequency (hf) when k w >= 1;
+ *  - a pair is admissible when |t|_inf >= 2 and, at an hf level, also
+ *    |c_X - c_Y| > k w^2, evaluated in FP64 as ((t.t) w) w > ((k w) w)^2;
+ *  - cones: each face of the cube [-1, 1]^3 split into m x m squares, m the
+ *    smallest power of two >= k w (m = 0, one cone, at an lf level); the cone
+ *    of a pair is the square hit along c_X - c_Y: face axis f = the first axis
+ *    of largest |t_i|, side s = (t_f < 0), on the other axes a < b the squares
+ *    i = min(floor((t_a + |t_f|) m / (2 |t_f|)), m - 1); cone
+ *    (2 f + s) m^2 + i_b m + i_a;
+ *  - lists (Alg. 1 on a uniform-depth octree, per level): Y is in the list of
+ *    (X, cone of X - Y) when the pair is admissible at this level and no pair
+ *    of their ancestors at levels 0 .. level - 1 is.
+ *
+ * m2l_dfmm_build_lists: the lists of `level` (cell width domain_width /
+ *   2^level, coordinates in [0, 2^level)^3, level <= 8, m <= 32).  CSR over
+ *   target expansions e = x * n_cones + c: il_offsets device
+ *   [ncells_tgt * n_cones + 1]; within an expansion the sources ascend in
+ *   linear cell index (x fastest), i.e. in source index when the source
+ *   cells are sorted that way (source cells must be distinct).  Three
+ *   calls: with il_offsets == NULL it only writes *n_cones; with
+ *   il_sources == NULL it writes *n_cones, the offsets and *nnz_out; then it
+ *   fills il_sources (device [nnz]).  Synchronous.  The source expansion of
+ *   an entry is y * n_cones + c.
+ * m2l_dfmm_plan_create: classifies the level's entries (t -> p(t), g(t)),
+ *   finds T_sym (the distinct p(t), lexicographic) and the class sizes n_p
+ *   (Sec. 4.2.3: not known before the lists), assembles the complex K_p at
+ *   the level's width in FP64 (and an FP32 copy) and buckets the entries.
+ *   Synchronous; allocates what it keeps; the level's arrays may be freed
+ *   afterwards.  Entries with |t|_inf < 2 or indices out of range:
+ *   M2L_EINVAL.
+ * m2l_dfmm_plan_info: |T_sym|, n_cones, nnz; host_tsym [nsym][3] and
+ *   host_np [nsym] when not NULL.
+ * m2l_dfmm_plan_apply: locals += M2L(multipoles), stream-ordered, no
+ *   allocation.  precision M2L_FP64 or M2L_FP32 (the product and the
+ *   accumulation; results added with atomics, so the summation order of a
+ *   target varies from run to run within rounding). */
+typedef struct {
+    int level;                   /* octree level, informational */
+    double width;                /* cell width w (> 0) */
+    int ncells_tgt, ncells_src;  /* cells; ncells_tgt * n_cones < 2^26 */
+    int n_cones;                 /* expansions per cell (>= 1) */
+    const int32_t *tgt_ijk;      /* device [ncells_tgt][3] */
+    const int32_t *src_ijk;      /* device [ncells_src][3] */
+    const int32_t *il_offsets;   /* device [ncells_tgt * n_cones + 1], CSR over target expansions */
+    const int32_t *il_sources;   /* device [nnz] source cells */
+    int nnz;
+} m2l_dlevel;
+typedef struct m2l_dplan m2l_dplan;
+m2l_status m2l_dfmm_build_lists(int level, double wavenumber, double domain_width, int ncells_tgt,
+                                const int32_t *tgt_ijk, int ncells_src, const int32_t *src_ijk, int *n_cones,
+                                int32_t *il_offsets, int32_t *il_sources, int64_t *nnz_out, void *stream);
+m2l_status m2l_dfmm_plan_create(int ell, double wavenumber, const m2l_dlevel *level, void *stream,
+                                m2l_dplan **out);
+m2l_status m2l_dfmm_plan_info(const m2l_dplan *plan, int *nsym, int *n_cones, int64_t *nnz, int32_t *host_tsym,
+                              int64_t *host_np);
+m2l_status m2l_dfmm_plan_apply(const m2l_dplan *plan, const void *multipoles, void *locals, int precision,
+                               void *stream);
+void m2l_dfmm_plan_free(m2l_dplan *plan);
+
+/* ---------------------------------------------------------------------
  * Interaction lists (Sec. 3.2, Alg. 1 for asymptotically smooth kernels):
  * Y is in the list of X when their parents are neighbours,
  * |floor(X/2) - floor(Y/2)|_inf <= 1, and |X - Y|_inf >= 2.  Sources of a

@@ -458,6 +458,7 @@ m2l_status fmm_build(m2l_fmm *f, const m2l_ops *const *ops, const T *xyz, cudaSt
     const int side = 1 << leaf;
     const size_t dense = (size_t)side * side * side;
     DevBuf lin, cnt, cursor, flag, pflag, pos;
+    ScratchGuard guard{&lin, &cnt, &cursor, &flag, &pflag, &pos};
     auto cleanup = [&]() { lin.release(); cnt.release(); cursor.release(); flag.release(); pflag.release(); pos.release(); };
     if ((st = f->perm.ensure((size_t)(n > 0 ? n : 1) * sizeof(int32_t))) != M2L_OK) return st;
     if ((st = f->start.ensure((dense + 1) * sizeof(int32_t))) != M2L_OK) return st;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <initializer_list>
 #include <string>
 
 #include "../../include/m2l.h"
@@ -63,6 +64,24 @@ struct DevBuf {
     m2l_status ensure(size_t need);
     void release();
     template <typename T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Releases scratch buffers on every return path of the scope that declares it
+// (cudaFree synchronises with the device, so work using them has finished).
+struct ScratchGuard {
+    DevBuf *bufs[24];
+    int n = 0;
+    ScratchGuard(std::initializer_list<DevBuf *> l)
+    {
+        for (DevBuf *b : l)
+            if (n < 24) bufs[n++] = b;
+    }
+    ~ScratchGuard()
+    {
+        for (int i = 0; i < n; ++i) bufs[i]->release();
+    }
+    ScratchGuard(const ScratchGuard &) = delete;
+    ScratchGuard &operator=(const ScratchGuard &) = delete;
 };
 
 // Output of the classification and bucketing (step a3).

@@ -89,6 +89,7 @@ extern "C" m2l_status m2l_build_lists(int ncells_tgt, const int32_t *tgt_ijk, in
     }
     cudaStream_t s = (cudaStream_t)stream;
     DevBuf ext, table, cnt, dup;
+    ScratchGuard guard{&ext, &table, &cnt, &dup};
     m2l_status st;
     if ((st = ext.ensure(2 * sizeof(int))) != M2L_OK) return st;
     if ((st = dup.ensure(sizeof(int))) != M2L_OK) return st;

@@ -29,6 +29,13 @@ class M2LError(RuntimeError):
         self.status = status
 
 
+class m2l_dlevel(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int), ("width", ctypes.c_double), ("ncells_tgt", ctypes.c_int),
+                ("ncells_src", ctypes.c_int), ("n_cones", ctypes.c_int), ("tgt_ijk", ctypes.c_void_p),
+                ("src_ijk", ctypes.c_void_p), ("il_offsets", ctypes.c_void_p), ("il_sources", ctypes.c_void_p),
+                ("nnz", ctypes.c_int)]
+
+
 class m2l_kernel(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int), ("c", ctypes.c_double)]
 
@@ -83,6 +90,10 @@ def lib():
             "m2l_sa_info": [P, P, P, P],
             "m2l_sa_copy_factors": [P, P, P, P, P],
             "m2l_sa_apply_level": [P, ctypes.POINTER(m2l_level), P, P, I, I, P],
+            "m2l_dfmm_build_lists": [I, D, D, I, P, I, P, P, P, P, P, P],
+            "m2l_dfmm_plan_create": [I, D, ctypes.POINTER(m2l_dlevel), P, ctypes.POINTER(P)],
+            "m2l_dfmm_plan_info": [P, P, P, P, P, P],
+            "m2l_dfmm_plan_apply": [P, P, P, I, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -98,6 +109,8 @@ def lib():
         L.m2l_fmm_free.restype = None
         L.m2l_sa_free.argtypes = [P]
         L.m2l_sa_free.restype = None
+        L.m2l_dfmm_plan_free.argtypes = [P]
+        L.m2l_dfmm_plan_free.restype = None
         L.m2l_last_error.argtypes = []
         L.m2l_last_error.restype = ctypes.c_char_p
         L.m2l_launch_count.argtypes = []
@@ -523,3 +536,90 @@ def m2l_sa_apply_level(sa: SA, level: Level, multipoles, locals_, precision="fp3
     _check("m2l_sa_apply_level", lib().m2l_sa_apply_level(
         sa.handle, ctypes.byref(level.struct), _dev_ptr(multipoles, tin, "multipoles"),
         _dev_ptr(locals_, tout, "locals"), p, int(bool(locals_fp64)), _stream_ptr(stream)))
+
+
+# ---------------------------------------------------------------- directional FMM (Helmholtz)
+def m2l_dfmm_build_lists(level, wavenumber, tgt_ijk, src_ijk=None, domain_width=2.0, stream=None):
+    """Directional far-field lists of one level: (n_cones, offsets [ntgt * n_cones + 1],
+    sources [nnz]) as device int32 tensors (CSR over target expansions x * n_cones + c)."""
+    import torch
+    if src_ijk is None:
+        src_ijk = tgt_ijk
+    for t, what in ((tgt_ijk, "tgt_ijk"), (src_ijk, "src_ijk")):
+        _dev_ptr(t, torch.int32, what)
+    nt, ns = int(tgt_ijk.shape[0]), int(src_ijk.shape[0])
+    C = ctypes.c_int()
+    nnz = ctypes.c_int64()
+    args = (int(level), float(wavenumber), float(domain_width), nt, _dev_ptr(tgt_ijk), ns, _dev_ptr(src_ijk),
+            ctypes.byref(C))
+    _check("m2l_dfmm_build_lists", lib().m2l_dfmm_build_lists(*args, None, None, ctypes.byref(nnz),
+                                                              _stream_ptr(stream)))
+    off = torch.empty(nt * C.value + 1, dtype=torch.int32, device=tgt_ijk.device)
+    _check("m2l_dfmm_build_lists", lib().m2l_dfmm_build_lists(*args, _dev_ptr(off), None, ctypes.byref(nnz),
+                                                              _stream_ptr(stream)))
+    src = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=tgt_ijk.device)
+    if nnz.value > 0:
+        _check("m2l_dfmm_build_lists", lib().m2l_dfmm_build_lists(*args, _dev_ptr(off), _dev_ptr(src),
+                                                                  ctypes.byref(nnz), _stream_ptr(stream)))
+    return C.value, off, src[:nnz.value]
+
+
+class DLevel:
+    """One level's directional lists (device arrays kept alive with the struct)."""
+
+    def __init__(self, width, tgt_ijk, src_ijk, n_cones, il_offsets, il_sources, level=0):
+        import torch
+        self.tgt_ijk, self.src_ijk, self.il_offsets, self.il_sources = tgt_ijk, src_ijk, il_offsets, il_sources
+        for name in ("tgt_ijk", "src_ijk", "il_offsets", "il_sources"):
+            _dev_ptr(getattr(self, name), torch.int32, name)
+        self.n_cones = int(n_cones)
+        self.struct = m2l_dlevel(int(level), float(width), int(tgt_ijk.shape[0]), int(src_ijk.shape[0]),
+                                 self.n_cones, tgt_ijk.data_ptr(), src_ijk.data_ptr(), il_offsets.data_ptr(),
+                                 il_sources.data_ptr(), int(il_sources.numel()))
+
+
+class DPlan:
+    """Owner of an m2l_dplan handle."""
+
+    def __init__(self, handle, ell, n_cones, ntgt, nsrc):
+        self.handle, self.ell, self.n_cones, self.ntgt, self.nsrc = handle, ell, n_cones, ntgt, nsrc
+        self.n3 = ell ** 3
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.m2l_dfmm_plan_free(h)
+
+
+def m2l_dfmm_plan_create(ell, wavenumber, level: DLevel, stream=None) -> DPlan:
+    h = ctypes.c_void_p()
+    _check("m2l_dfmm_plan_create", lib().m2l_dfmm_plan_create(int(ell), float(wavenumber), ctypes.byref(level.struct),
+                                                              _stream_ptr(stream), ctypes.byref(h)))
+    return DPlan(h, ell, level.n_cones, level.struct.ncells_tgt, level.struct.ncells_src)
+
+
+def m2l_dfmm_plan_info(plan: DPlan):
+    """(T_sym [nsym, 3] int32, n_p [nsym] int64, n_cones, nnz) on the host."""
+    nsym, C, nnz = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+    _check("m2l_dfmm_plan_info", lib().m2l_dfmm_plan_info(plan.handle, ctypes.byref(nsym), ctypes.byref(C),
+                                                          ctypes.byref(nnz), None, None))
+    tsym = np.zeros((max(nsym.value, 1), 3), dtype=np.int32)
+    n_p = np.zeros(max(nsym.value, 1), dtype=np.int64)
+    _check("m2l_dfmm_plan_info", lib().m2l_dfmm_plan_info(plan.handle, None, None, None, tsym.ctypes.data,
+                                                          n_p.ctypes.data))
+    return tsym[:nsym.value], n_p[:nsym.value], C.value, nnz.value
+
+
+def m2l_dfmm_plan_apply(plan: DPlan, multipoles, locals_, precision="fp32", stream=None):
+    """locals_ += M2L(multipoles); complex tensors [ncells * n_cones, ell^3] (or
+    [ncells, n_cones, ell^3]), complex128 for "fp64", complex64 for "fp32"."""
+    import torch
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    dt = {M2L_FP64: torch.complex128, M2L_FP32: torch.complex64}.get(p)
+    if dt is None:
+        raise ValueError("the directional apply runs in fp64 or fp32")
+    for t, n, what in ((multipoles, plan.nsrc, "multipoles"), (locals_, plan.ntgt, "locals")):
+        if t.numel() != n * plan.n_cones * plan.n3:
+            raise ValueError("%s must hold %d x %d x %d values" % (what, n, plan.n_cones, plan.n3))
+    _check("m2l_dfmm_plan_apply", lib().m2l_dfmm_plan_apply(plan.handle, _dev_ptr(multipoles, dt, "multipoles"),
+                                                            _dev_ptr(locals_, dt, "locals"), p, _stream_ptr(stream)))

@@ -68,6 +68,11 @@ def test_null_handles_rejected(lib):
     assert lib.m2l_sa_copy_factors(None, None, None, None, None) == m2l.M2L_EINVAL
     assert lib.m2l_sa_apply_level(None, None, None, None, 1, 0, None) == m2l.M2L_EINVAL
     lib.m2l_sa_free(None)
+    assert lib.m2l_dfmm_build_lists(-1, 1.0, 2.0, 0, None, 0, None, None, None, None, None, None) == m2l.M2L_EINVAL
+    assert lib.m2l_dfmm_plan_create(4, 1.0, None, None, None) == m2l.M2L_EINVAL
+    assert lib.m2l_dfmm_plan_info(None, None, None, None, None, None) == m2l.M2L_EINVAL
+    assert lib.m2l_dfmm_plan_apply(None, None, None, 1, None) == m2l.M2L_EINVAL
+    lib.m2l_dfmm_plan_free(None)
     lib.m2l_fmm_free(None)
     lib.m2l_ops_free(None)
     lib.m2l_plan_free(None)

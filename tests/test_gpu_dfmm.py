@@ -1,0 +1,159 @@
+"""The directional (dFMM) M2L on the GPU (m2l_dfmm_*) against the oracle:
+lists bit for bit, T_sym and the class sizes n_p exactly, the complex M2L
+element by element (FP64 within 1e-12, FP32 within 2e-6), on the sphere of
+the paper's dFMM runs (k times the domain width = 64) and on a small tree
+that also has low-frequency levels."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+d = oracle.dfmm
+K_SPHERE = 32.0      # the paper's k = 1 in a box of side 64, on the unit domain [-1, 1]^3
+
+
+@pytest.fixture(scope="module")
+def m2l():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as g
+    g.build()
+    from paper_1210_7292_gb300 import m2l as mod
+    return mod
+
+
+def _cells(n, level, seed=21):
+    from paper_1210_7292_gb300 import synth
+    pts, _ = synth.sphere_surface(n, seed=seed)
+    return synth.occupied_cells(pts, level)
+
+
+def _gpu_level(m2l, cells, level, k):
+    ijk = torch.from_numpy(cells).cuda()
+    C, off, src = m2l.m2l_dfmm_build_lists(level, k, ijk)
+    return m2l.DLevel(d.level_width(level, 2.0), ijk, ijk, C, off, src, level)
+
+
+@pytest.mark.parametrize("n,k,levels", [(30000, K_SPHERE, [2, 3, 4, 5, 6]), (3000, 8.0, [2, 3, 4, 5, 6])])
+def test_lists_bit_exact(m2l, n, k, levels):
+    for L in levels:
+        cells = _cells(n, L)
+        lv = _gpu_level(m2l, cells, L, k)
+        C, off, src = d.directional_lists(cells, L, k, 2.0)
+        assert lv.n_cones == C, L
+        assert np.array_equal(lv.il_offsets.cpu().numpy(), off), L
+        assert np.array_equal(lv.il_sources.cpu().numpy(), src), L
+
+
+def _oracle_classes(cells, C, off, src):
+    x = np.repeat(np.arange(len(off) - 1) // C, np.diff(off))
+    t = cells[x].astype(np.int64) - cells[src].astype(np.int64)
+    can = -np.sort(-np.abs(t), axis=1)
+    tsym, n_p = np.unique(can, axis=0, return_counts=True)
+    return tsym, n_p
+
+
+@pytest.mark.parametrize("n,level", [(30000, 3), (30000, 4), (30000, 5)])
+def test_plan_classes_exact(m2l, n, level):
+    cells = _cells(n, level)
+    lv = _gpu_level(m2l, cells, level, K_SPHERE)
+    plan = m2l.m2l_dfmm_plan_create(4, K_SPHERE, lv)
+    tsym, n_p, C, nnz = m2l.m2l_dfmm_plan_info(plan)
+    ref_tsym, ref_np = _oracle_classes(cells, lv.n_cones, lv.il_offsets.cpu().numpy(), lv.il_sources.cpu().numpy())
+    assert C == lv.n_cones and nnz == lv.struct.nnz
+    assert np.array_equal(tsym, ref_tsym) and np.array_equal(n_p, ref_np)
+    assert [tuple(t) for t in tsym] == d.t_sym_of_lists(cells, cells, lv.il_offsets.cpu().numpy(),
+                                                       lv.il_sources.cpu().numpy(), C)
+
+
+def _sampled_oracle(ell, k, level, cells, C, off, src, W, rows):
+    """Oracle M2L of the sampled target expansions only (the other rows get empty lists)."""
+    keep = np.zeros(len(off) - 1, dtype=bool)
+    keep[rows] = True
+    counts = np.where(keep, np.diff(off), 0)
+    off_s = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    src_s = np.concatenate([src[off[e]:off[e + 1]] for e in range(len(off) - 1) if keep[e]] or [np.zeros(0, np.int32)])
+    F = d.dfmm_m2l_apply(ell, k, level, cells, cells, C, off_s, src_s.astype(np.int32), W)
+    return F[rows]
+
+
+def _run(m2l, ell, k, level, cells, prec, seed=7):
+    lv = _gpu_level(m2l, cells, level, k)
+    plan = m2l.m2l_dfmm_plan_create(ell, k, lv)
+    C, n3 = lv.n_cones, ell ** 3
+    g = np.random.default_rng(seed)
+    W = g.standard_normal((len(cells) * C, n3)) + 1j * g.standard_normal((len(cells) * C, n3))
+    F0 = g.standard_normal((len(cells) * C, n3)) + 1j * g.standard_normal((len(cells) * C, n3))
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    Wd = torch.from_numpy(W).to("cuda", dt)
+    Fd = torch.from_numpy(F0).to("cuda", dt)
+    m2l.m2l_dfmm_plan_apply(plan, Wd, Fd, prec)
+    torch.cuda.synchronize()
+    return lv, W, F0, Fd.to(torch.complex128).cpu().numpy()
+
+
+@pytest.mark.parametrize("ell,k,n,level", [(3, K_SPHERE, 30000, 4), (4, K_SPHERE, 20000, 5), (5, K_SPHERE, 8000, 3),
+                                           (4, 8.0, 3000, 5), (2, 8.0, 3000, 4)])
+def test_apply_fp64_matches_oracle(m2l, ell, k, n, level):
+    cells = _cells(n, level)
+    lv, W, F0, got = _run(m2l, ell, k, level, cells, "fp64")
+    off, src = lv.il_offsets.cpu().numpy(), lv.il_sources.cpu().numpy()
+    nz = np.flatnonzero(np.diff(off) > 0)
+    rows = np.sort(np.random.default_rng(1).choice(nz, min(200, len(nz)), replace=False))
+    ref = _sampled_oracle(ell, k, level, cells, lv.n_cones, off, src, W, rows)
+    err = oracle.rel_l2(got[rows] - F0[rows], ref)
+    print("dFMM fp64 ell=%d k=%g level=%d: %d expansions, %d entries, rel L2 %.2e" % (
+        ell, k, level, len(off) - 1, len(src), err))
+    assert err < 1e-12, err
+    # rows without entries are untouched
+    empty = np.flatnonzero(np.diff(off) == 0)[:500]
+    assert np.array_equal(got[empty], F0[empty])
+
+
+@pytest.mark.parametrize("ell,level", [(5, 4), (4, 6)])
+def test_apply_fp32_matches_fp64(m2l, ell, level):
+    cells = _cells(30000, level)
+    _, _, F0, g64 = _run(m2l, ell, K_SPHERE, level, cells, "fp64")
+    _, _, _, g32 = _run(m2l, ell, K_SPHERE, level, cells, "fp32")
+    err = oracle.rel_l2(g32 - F0, g64 - F0)
+    print("dFMM fp32 vs fp64 ell=%d level=%d: %.2e" % (ell, level, err))
+    assert err < 2e-6, err
+
+
+def test_paper_sphere_level4_sampled(m2l):
+    """The full dFMM workload's largest level (168,931 points, level 4: 96 cones,
+    1.2 M entries, ell = 5) in the bench's configuration, sampled against the oracle."""
+    cells = _cells(168931, 4)
+    lv, W, F0, got = _run(m2l, 5, K_SPHERE, 4, cells, "fp32")
+    assert lv.struct.nnz == 1212408
+    off, src = lv.il_offsets.cpu().numpy(), lv.il_sources.cpu().numpy()
+    nz = np.flatnonzero(np.diff(off) > 0)
+    rows = np.sort(np.random.default_rng(2).choice(nz, 64, replace=False))
+    ref = _sampled_oracle(5, K_SPHERE, 4, cells, lv.n_cones, off, src, W, rows)
+    err = oracle.rel_l2(got[rows] - F0[rows], ref)
+    assert err < 2e-6, err
+
+
+def test_bad_lists_and_empty_level(m2l):
+    cells = _cells(3000, 4)
+    ijk = torch.from_numpy(cells).cuda()
+    C, off, src = m2l.m2l_dfmm_build_lists(4, K_SPHERE, ijk)
+    bad = src.clone()
+    bad[0] = int(np.flatnonzero(np.diff(off.cpu().numpy()) > 0)[0] // C)   # the target itself: t = 0
+    lv = m2l.DLevel(d.level_width(4, 2.0), ijk, ijk, C, off, bad, 4)
+    with pytest.raises(m2l.M2LError) as ei:
+        m2l.m2l_dfmm_plan_create(4, K_SPHERE, lv)
+    assert ei.value.status == m2l.M2L_EINVAL
+    # cells outside the level's grid
+    with pytest.raises(m2l.M2LError):
+        m2l.m2l_dfmm_build_lists(2, K_SPHERE, ijk)
+    # an empty level
+    e = torch.zeros((0, 3), dtype=torch.int32, device="cuda")
+    C0, off0, src0 = m2l.m2l_dfmm_build_lists(4, K_SPHERE, e)
+    assert off0.cpu().tolist() == [0] and src0.numel() == 0
+    plan = m2l.m2l_dfmm_plan_create(4, K_SPHERE, m2l.DLevel(d.level_width(4, 2.0), e, e, C0, off0, src0, 4))
+    z = torch.zeros((0, C0, 64), dtype=torch.complex64, device="cuda")
+    m2l.m2l_dfmm_plan_apply(plan, z, z, "fp32")
+    torch.cuda.synchronize()
