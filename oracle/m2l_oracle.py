@@ -357,6 +357,79 @@ def lowrank_operator_table(ops: np.ndarray, eps: float):
 
 
 # --------------------------------------------------------------------------
+# ACA followed by a truncated SVD (Sec. 4.1 and Sec. 5: the cheaper route to
+# the factors of Eq. (20); the algorithm is Bebendorf's partially pivoted ACA)
+# --------------------------------------------------------------------------
+ACA_EPS_FACTOR = 0.01   # reading: ACA stops at eps_ACA = 0.01 eps before the truncated SVD
+
+
+def aca(K: np.ndarray, eps_aca: float, kmax: int = None, return_pivots: bool = False):
+    """Adaptive cross approximation with partial pivoting, K ~ sum_k u_k v_k^T.
+
+    Steps, in order: take pivot row i (row 0 first), form its residual row
+    r = K[i, :] - sum_l u_l[i] v_l; take the column j of largest |r_j| (the
+    first on ties); if r_j = 0 the row is exhausted: move to the first unused
+    row without adding a term; else v_k = r / r_j and u_k = the residual of
+    column j.  The Frobenius norm of the approximant S_k is updated
+    incrementally; stop when |u_k| |v_k| <= eps_aca |S_k|_F.  The next pivot
+    row is the unused row of largest |u_k[i]| (the first on ties).
+
+    Returns (U [m, k], V [n, k]) and, with return_pivots, the pivot rows and
+    columns of the k terms.
+    """
+    K = np.asarray(K, dtype=np.float64)
+    m, n = K.shape
+    kmax = min(m, n) if kmax is None else kmax
+    us, vs, piv = [], [], []
+    used = np.zeros(m, dtype=bool)
+    i = 0
+    norm2 = 0.0
+    while len(us) < kmax:
+        used[i] = True
+        r = K[i, :].copy()
+        for u, v in zip(us, vs):
+            r -= u[i] * v
+        j = int(np.argmax(np.abs(r)))
+        if r[j] == 0.0:
+            free = np.flatnonzero(~used)
+            if len(free) == 0:
+                break
+            i = int(free[0])
+            continue
+        v = r / r[j]
+        u = K[:, j].copy()
+        for ul, vl in zip(us, vs):
+            u -= vl[j] * ul
+        cross = sum((ul @ u) * (vl @ v) for ul, vl in zip(us, vs))
+        uu, vv = float(u @ u), float(v @ v)
+        norm2 += 2.0 * cross + uu * vv
+        us.append(u)
+        vs.append(v)
+        piv.append((i, j))
+        if np.sqrt(uu * vv) <= eps_aca * np.sqrt(norm2):
+            break
+        cand = np.where(used, -1.0, np.abs(u))
+        if cand.max() < 0.0:
+            break
+        i = int(np.argmax(cand))
+    U = np.stack(us, axis=1) if us else np.zeros((m, 0))
+    V = np.stack(vs, axis=1) if vs else np.zeros((n, 0))
+    return (U, V, piv) if return_pivots else (U, V)
+
+
+def aca_lowrank(K: np.ndarray, eps: float):
+    """ACA at eps_ACA = ACA_EPS_FACTOR eps, then the truncated SVD of the
+    approximant (QR of both factors, SVD of the small core), truncated with the
+    criterion of Eq. (20).  Returns (U_t = U_r Sigma_r, V_t, rank, aca_terms)."""
+    Ua, Va = aca(K, ACA_EPS_FACTOR * eps)
+    Qu, Ru = np.linalg.qr(Ua)
+    Qv, Rv = np.linalg.qr(Va)
+    W, s, Zt = np.linalg.svd(Ru @ Rv.T)
+    r = max(1, truncation_rank(s, eps))
+    return (Qu @ W[:, :r]) * s[None, :r], Qv @ Zt[:r, :].T, r, Ua.shape[1]
+
+
+# --------------------------------------------------------------------------
 # single low-rank approximation (SA) and its recompression (SArcmp), Sec. 4.1
 # --------------------------------------------------------------------------
 def sa_factors(ops: np.ndarray, eps: float):

@@ -472,3 +472,38 @@ def test_sarcmp_recompression():
         else:
             assert np.array_equal(C2[sl], sa["C"][sl])
     assert n_re > 0
+
+
+# ---------------------------------------------------------------- ACA + truncated SVD
+def test_aca_recovers_an_exact_low_rank_matrix():
+    g = np.random.default_rng(11)
+    K = g.standard_normal((60, 7)) @ g.standard_normal((7, 50))
+    U, V = o.aca(K, 1e-14)
+    assert U.shape[1] <= 8
+    assert np.abs(U @ V.T - K).max() < 1e-11 * np.abs(K).max()
+
+
+def test_aca_interpolates_its_pivot_rows_and_columns():
+    """A cross approximation reproduces K exactly on every pivot row and column."""
+    K = o.operator_for_t(5, 0, 0.0, 3, (3, 1, 0))
+    U, V, piv = o.aca(K, 1e-6, return_pivots=True)
+    S = U @ V.T
+    scale = np.abs(K).max()
+    for i, j in piv:
+        assert np.abs(S[i, :] - K[i, :]).max() < 1e-12 * scale
+        assert np.abs(S[:, j] - K[:, j]).max() < 1e-12 * scale
+
+
+@pytest.mark.parametrize("ell,kind,eps", [(5, 0, 1e-5), (7, 1, 1e-7), (6, 2, 1e-6), (3, 0, 1e-3)])
+def test_aca_then_svd_gives_the_svd_ranks(ell, kind, eps):
+    """Sec. 5: ACA followed by a truncated SVD ends with the same ranks as the SVD;
+    the error stays within the truncation bound eps s_1 (spectral)."""
+    c = 0.01 if kind == 2 else 0.0
+    for t in o.t_sym_list():
+        K = o.operator_for_t(ell, kind, c, 3, t)
+        _, _, r = o.lowrank(K, eps)
+        U, V, ra, k = o.aca_lowrank(K, eps)
+        assert ra == r, (t, r, ra)
+        s1 = np.linalg.norm(K, 2)
+        assert np.linalg.norm(K - U @ V.T, 2) <= 1.01 * eps * s1
+        assert k < K.shape[0]
