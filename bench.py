@@ -440,19 +440,24 @@ def roofline(precision, achieved_tflops, peaks, src_kind):
 
 
 def precompute_times(m2l, device, reps=3):
-    """Wall time of m2l_precompute (step a1: the 16 operators, tables and, with
-    eps > 0, the per-operator truncated SVD) for the bench's order and for the
-    mixed-precision workload's ell = 7, 1/r^4, eps = 1e-7."""
+    """Wall time of the precompute (step a1: the 16 operators, tables and, with
+    eps > 0, their low-rank factors by truncated SVD or by ACA + truncated SVD)
+    at the bench's order and at the mixed-precision workload's ell = 7, 1/r^4,
+    eps = 1e-7."""
     import torch
     out = {}
-    for name, kind, ell, eps in (("full_ell5_inv_r", m2l.M2L_K_INV_R, ELL, 0.0),
-                                 ("svd_ell7_inv_r4_eps1e-7", m2l.M2L_K_INV_R4, 7, 1e-7)):
-        m2l.m2l_precompute(kind, ell, eps)   # first call: module load, workspace
+    svd, aca = m2l.m2l_precompute, m2l.m2l_precompute_aca
+    for name, fn, kind, ell, eps in (("full_ell5_inv_r", svd, m2l.M2L_K_INV_R, ELL, 0.0),
+                                     ("svd_ell5_inv_r_eps1e-5", svd, m2l.M2L_K_INV_R, ELL, 1e-5),
+                                     ("aca_ell5_inv_r_eps1e-5", aca, m2l.M2L_K_INV_R, ELL, 1e-5),
+                                     ("svd_ell7_inv_r4_eps1e-7", svd, m2l.M2L_K_INV_R4, 7, 1e-7),
+                                     ("aca_ell7_inv_r4_eps1e-7", aca, m2l.M2L_K_INV_R4, 7, 1e-7)):
+        fn(kind, ell, eps)   # first call: module load, workspace
         ts = []
         for _ in range(reps):
             torch.cuda.synchronize(device)
             t0 = time.perf_counter()
-            ops = m2l.m2l_precompute(kind, ell, eps)
+            ops = fn(kind, ell, eps)
             torch.cuda.synchronize(device)
             ts.append(1e3 * (time.perf_counter() - t0))
             del ops

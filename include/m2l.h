@@ -113,6 +113,23 @@ typedef struct {
  * for out-of-range arguments, M2L_ENOMEM, M2L_ECUDA. */
 m2l_status m2l_precompute(m2l_kernel kernel, int ell, double eps, double width, m2l_ops **out);
 
+/* m2l_precompute with the low-rank factors (eps > 0) computed by adaptive
+ * cross approximation followed by a truncated SVD (Sec. 4.1 and Sec. 5, the
+ * cheaper precompute; Bebendorf's ACA with partial pivoting), on the device:
+ * ACA of each K_p stopped at |u_k| |v_k| <= 0.01 eps |S_k|_F (pivot row 0
+ * first; the column of the largest residual; the next row of the largest
+ * |u_k| among unused rows; first index on ties), QR of both factor sets
+ * (Gram-Schmidt with one re-orthogonalisation), one-sided Jacobi SVD of the
+ * small core, truncation with the criterion of m2l_precompute.  The factors
+ * have the layout of m2l_precompute's (U = U_K Sigma, V = V_K) and every apply
+ * entry point uses them alike.  With eps = 0 it equals m2l_precompute.
+ * Errors as m2l_precompute; M2L_ECUDA if a Jacobi SVD does not converge. */
+m2l_status m2l_precompute_aca(m2l_kernel kernel, int ell, double eps, double width, m2l_ops **out);
+
+/* Per operator p: ACA terms before the recompression and Jacobi sweeps, for
+ * ops from m2l_precompute_aca with eps > 0 (else M2L_EINVAL); NULL skips one. */
+m2l_status m2l_ops_aca_info(const m2l_ops *ops, int32_t *aca_terms16, int32_t *jacobi_sweeps16);
+
 /* Re-runs the device assembly of the full-rank operators and tables of
  * `ops` into its existing buffers (no allocation), stream-ordered.  Used to
  * time the precompute as part of a step.  M2L_EUNSUPPORTED for ops built with

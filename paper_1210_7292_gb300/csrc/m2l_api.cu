@@ -124,6 +124,10 @@ static m2l_status dispatch(const m2l_ops *ops, const Buckets &b, const void *in,
 
 using namespace m2l;
 
+namespace {
+m2l_status precompute_impl(m2l_kernel kernel, int ell, double eps, double width, int aca, m2l_ops **out);
+}
+
 extern "C" {
 
 const char *m2l_last_error(void) { return g_err; }
@@ -131,6 +135,30 @@ const char *m2l_last_error(void) { return g_err; }
 int64_t m2l_launch_count(void) { return (int64_t)g_launches.load(); }
 
 m2l_status m2l_precompute(m2l_kernel kernel, int ell, double eps, double width, m2l_ops **out)
+{
+    return precompute_impl(kernel, ell, eps, width, 0, out);
+}
+
+m2l_status m2l_precompute_aca(m2l_kernel kernel, int ell, double eps, double width, m2l_ops **out)
+{
+    return precompute_impl(kernel, ell, eps, width, 1, out);
+}
+
+m2l_status m2l_ops_aca_info(const m2l_ops *ops, int32_t *aca_terms16, int32_t *jacobi_sweeps16)
+{
+    if (!ops) { set_error("null ops"); return M2L_EINVAL; }
+    if (ops->lowrank_method != 1) { set_error("ops not built by m2l_precompute_aca with eps > 0"); return M2L_EINVAL; }
+    for (int p = 0; p < 16; ++p) {
+        if (aca_terms16) aca_terms16[p] = ops->aca_terms[p];
+        if (jacobi_sweeps16) jacobi_sweeps16[p] = ops->jacobi_sweeps[p];
+    }
+    return M2L_OK;
+}
+
+}  // extern "C"
+
+namespace {
+m2l_status precompute_impl(m2l_kernel kernel, int ell, double eps, double width, int aca, m2l_ops **out)
 {
     g_err[0] = 0;
     if (!out) { set_error("null output pointer"); return M2L_EINVAL; }
@@ -170,7 +198,10 @@ m2l_status m2l_precompute(m2l_kernel kernel, int ell, double eps, double width, 
     }
     for (int p = 0; p < 16; ++p) ops->ranks[p] = n3;
     ops->rmax = n3;
-    if (st == M2L_OK && eps > 0.0) st = lowrank_factors(ops);
+    if (st == M2L_OK && eps > 0.0) {
+        ops->lowrank_method = aca ? 1 : 0;
+        st = aca ? lowrank_factors_aca(ops, ops->aca_terms, ops->jacobi_sweeps) : lowrank_factors(ops);
+    }
     if (st != M2L_OK) {
         m2l_ops_free(ops);
         return st;
@@ -178,6 +209,9 @@ m2l_status m2l_precompute(m2l_kernel kernel, int ell, double eps, double width, 
     *out = ops;
     return M2L_OK;
 }
+}  // namespace
+
+extern "C" {
 
 m2l_status m2l_ops_rebuild(m2l_ops *ops, void *stream)
 {

@@ -126,6 +126,9 @@ struct m2l_ops {
     m2l::Layout simt64, simt32, lr64, lr32, tc_tf32, tc_bf16x3, tc_tf32x3;
     mutable m2l::Buckets ws;  // workspace of m2l_apply_level
     mutable double ws_scale = 1.0;  // scale of the level last classified into ws
+    int lowrank_method = 0;   // 0: truncated SVD, 1: ACA + truncated SVD
+    int aca_terms[16] = {0};  // ACA terms before the recompression (method 1)
+    int jacobi_sweeps[16] = {0};
     int *d_status = nullptr;  // device status word
     int debug_flags = 0;      // M2L_DEBUG_* test switches
 };
@@ -144,6 +147,7 @@ namespace m2l {
 m2l_status build_tables(m2l_ops *ops, cudaStream_t s);
 m2l_status assemble_operators(m2l_ops *ops, cudaStream_t s);
 m2l_status lowrank_factors(m2l_ops *ops);
+m2l_status lowrank_factors_aca(m2l_ops *ops, int *aca_terms, int *jacobi_sweeps);
 m2l_status prepare_simt_layout(const m2l_ops *ops, int fp64, cudaStream_t s);
 int simt_kpad(int n3);
 int simt_mpad(int n3);

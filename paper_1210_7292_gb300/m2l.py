@@ -90,6 +90,8 @@ def lib():
             "m2l_sa_info": [P, P, P, P],
             "m2l_sa_copy_factors": [P, P, P, P, P],
             "m2l_sa_apply_level": [P, ctypes.POINTER(m2l_level), P, P, I, I, P],
+            "m2l_precompute_aca": [m2l_kernel, I, D, D, ctypes.POINTER(P)],
+            "m2l_ops_aca_info": [P, P, P],
             "m2l_dfmm_build_lists": [I, D, D, I, P, I, P, P, P, P, P, P],
             "m2l_dfmm_plan_create": [I, D, ctypes.POINTER(m2l_dlevel), P, ctypes.POINTER(P)],
             "m2l_dfmm_plan_info": [P, P, P, P, P, P],
@@ -183,6 +185,22 @@ def m2l_precompute(kernel_type, ell, eps=0.0, width=0.0, c=0.0) -> Ops:
     _check("m2l_precompute", lib().m2l_precompute(m2l_kernel(int(kernel_type), float(c)), int(ell), float(eps),
                                                   float(width), ctypes.byref(h)))
     return Ops(h, int(ell))
+
+
+def m2l_precompute_aca(kernel_type, ell, eps=0.0, width=0.0, c=0.0) -> Ops:
+    """m2l_precompute with the low-rank factors from ACA + truncated SVD."""
+    h = ctypes.c_void_p()
+    _check("m2l_precompute_aca", lib().m2l_precompute_aca(m2l_kernel(int(kernel_type), float(c)), int(ell),
+                                                          float(eps), float(width), ctypes.byref(h)))
+    return Ops(h, int(ell))
+
+
+def m2l_ops_aca_info(ops: Ops):
+    """(ACA terms [16], Jacobi sweeps [16]) of ops from m2l_precompute_aca."""
+    terms = np.zeros(16, dtype=np.int32)
+    sweeps = np.zeros(16, dtype=np.int32)
+    _check("m2l_ops_aca_info", lib().m2l_ops_aca_info(ops.handle, terms.ctypes.data, sweeps.ctypes.data))
+    return terms, sweeps
 
 
 def m2l_ops_rebuild(ops: Ops, stream=None):

@@ -46,9 +46,10 @@ def test_precompute_rejects_bad_arguments_on_host(lib):
     from paper_1210_7292_gb300 import m2l
     for kt, ell, eps, width in [(0, 1, 0.0, 0.0), (0, 9, 0.0, 0.0), (7, 4, 0.0, 0.0), (0, 4, 1.5, 0.0),
                                 (0, 4, -1.0, 0.0), (2, 4, 0.0, 0.0), (2, 4, 0.0, -1.0)]:
-        with pytest.raises(m2l.M2LError) as ei:
-            m2l.m2l_precompute(kt, ell, eps, width)
-        assert ei.value.status == m2l.M2L_EINVAL
+        for fn in (m2l.m2l_precompute, m2l.m2l_precompute_aca):
+            with pytest.raises(m2l.M2LError) as ei:
+                fn(kt, ell, eps, width)
+            assert ei.value.status == m2l.M2L_EINVAL
         assert m2l.m2l_last_error()
 
 
@@ -73,6 +74,7 @@ def test_null_handles_rejected(lib):
     assert lib.m2l_dfmm_plan_info(None, None, None, None, None, None) == m2l.M2L_EINVAL
     assert lib.m2l_dfmm_plan_apply(None, None, None, 1, None) == m2l.M2L_EINVAL
     lib.m2l_dfmm_plan_free(None)
+    assert lib.m2l_ops_aca_info(None, None, None) == m2l.M2L_EINVAL
     lib.m2l_fmm_free(None)
     lib.m2l_ops_free(None)
     lib.m2l_plan_free(None)
