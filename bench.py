@@ -748,6 +748,32 @@ def run_apply_only(args):
     return 0
 
 
+def run_dfmm_apply_only(args):
+    """The directional M2L of the dFMM workload's level 5 (ell = 5, FP32) alone,
+    three launches, for profiler captures of its apply kernel."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_1210_7292_gb300 import m2l, synth
+    device = torch.device("cuda", 0)
+    pts, _ = synth.sphere_surface(DFMM_PARTICLES, seed=21)
+    L = 5
+    ijk = torch.from_numpy(synth.occupied_cells(pts, L)).to(device)
+    C, off, src = m2l.m2l_dfmm_build_lists(L, DFMM_K, ijk)
+    plan = m2l.m2l_dfmm_plan_create(ELL, DFMM_K, m2l.DLevel(2.0 / (1 << L), ijk, ijk, C, off, src, L))
+    n = ijk.shape[0] * C * ELL ** 3
+    W = torch.complex(torch.randn(n, device=device), torch.randn(n, device=device))
+    F = torch.zeros_like(W)
+    for _ in range(3):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        m2l.m2l_dfmm_plan_apply(plan, W, F, "fp32")
+        e.record()
+        torch.cuda.synchronize()
+        log("dFMM level-5 apply (fp32, %d interactions): %.3f ms" % (src.numel(), s.elapsed_time(e)))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -761,6 +787,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the extra precisions and the CPU baseline")
     ap.add_argument("--apply-only", action="store_true",
                     help="run three level-5 apply launches only (for profiler captures)")
+    ap.add_argument("--dfmm-apply-only", action="store_true",
+                    help="run three directional level-5 apply launches only (for profiler captures)")
     args = ap.parse_args()
     args.compare = [p for p in args.compare.split(",") if p]
     if args.warmup < 3:
@@ -770,6 +798,8 @@ def main():
         return run_reference(args)
     if args.apply_only:
         return run_apply_only(args)
+    if args.dfmm_apply_only:
+        return run_dfmm_apply_only(args)
     return run_ours(args)
 
 
