@@ -353,11 +353,14 @@ template <> struct CT<float> { using V = float2; };
 template <> struct CT<double> { using V = double2; };
 
 // Tiles of NT interactions of one class: Bs [n3][NT + 1] gathered multipoles,
-// As [16][64] a slice of 64 operator rows, Cs [64][NT + 1] results.
+// As [16][65] a slice of 64 operator rows (padded: the slice is written along
+// k), Cs [64][NT + 1] results.
+constexpr int kDLdA = 65;
+
 template <typename T>
 size_t d_apply_smem(int n3, int NT)
 {
-    return ((size_t)n3 * (NT + 1) + 16 * 64 + 64 * (NT + 1)) * sizeof(typename CT<T>::V);
+    return ((size_t)n3 * (NT + 1) + 16 * kDLdA + 64 * (NT + 1)) * sizeof(typename CT<T>::V);
 }
 
 template <typename T, int NT>
@@ -372,7 +375,7 @@ d_apply_kernel(int n3, int ntiles, const int4 *__restrict__ tiles, const int2 *_
     extern __shared__ __align__(16) unsigned char d_smem[];
     V *Bs = reinterpret_cast<V *>(d_smem);
     V *As = Bs + (size_t)n3 * LD;
-    V *Cs = As + 16 * 64;
+    V *Cs = As + 16 * kDLdA;
     __shared__ int2 s_rec[NT];
     const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -402,21 +405,34 @@ d_apply_kernel(int n3, int ntiles, const int4 *__restrict__ tiles, const int2 *_
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int q = 0; q < NJ; ++q) acc_re[i][q] = acc_im[i][q] = T(0);
-            for (int k0 = 0; k0 < n3; k0 += 16) {
-                for (int idx = threadIdx.x; idx < 64 * 16; idx += blockDim.x) {
+            // the 64 x 16 operator slice: four elements per thread, the next slice
+            // loaded into registers while the current one is multiplied
+            constexpr int kPer = 64 * 16 / kDThreads;
+            V pre[kPer];
+            auto load_slice = [&](int k0) {
+#pragma unroll
+                for (int u = 0; u < kPer; ++u) {
+                    const int idx = threadIdx.x + u * kDThreads;
                     const int i = idx / 16, kk = idx % 16;
-                    V a;
-                    a.x = T(0);
-                    a.y = T(0);
-                    if (r0 + i < n3 && k0 + kk < n3) a = Kp[(size_t)(r0 + i) * n3 + k0 + kk];
-                    As[kk * 64 + i] = a;
+                    pre[u].x = T(0);
+                    pre[u].y = T(0);
+                    if (r0 + i < n3 && k0 + kk < n3) pre[u] = Kp[(size_t)(r0 + i) * n3 + k0 + kk];
+                }
+            };
+            load_slice(0);
+            for (int k0 = 0; k0 < n3; k0 += 16) {
+#pragma unroll
+                for (int u = 0; u < kPer; ++u) {
+                    const int idx = threadIdx.x + u * kDThreads;
+                    As[(idx % 16) * kDLdA + idx / 16] = pre[u];
                 }
                 __syncthreads();
+                if (k0 + 16 < n3) load_slice(k0 + 16);
                 const int kmax = min(16, n3 - k0);
                 for (int kk = 0; kk < kmax; ++kk) {
                     V a[4], b[NJ];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) a[i] = As[kk * 64 + tr + 16 * i];
+                    for (int i = 0; i < 4; ++i) a[i] = As[kk * kDLdA + tr + 16 * i];
 #pragma unroll
                     for (int q = 0; q < NJ; ++q) b[q] = Bs[(k0 + kk) * LD + tc + 16 * q];
 #pragma unroll
@@ -490,7 +506,7 @@ void dplan_release(m2l_dplan *p)
 int pick_nt(int n3, size_t esz2)
 {
     for (int nt : {64, 32, 16}) {
-        const size_t smem = ((size_t)n3 * (nt + 1) + 16 * 64 + 64 * (nt + 1)) * esz2;
+        const size_t smem = ((size_t)n3 * (nt + 1) + 16 * kDLdA + 64 * (nt + 1)) * esz2;
         if ((int)smem + 1024 <= max_smem_optin()) return nt;   // + the static tile records
     }
     return 0;
