@@ -585,6 +585,64 @@ def dfmm_m2l(m2l, device, reps=5):
     return out
 
 
+def config3_levels(m2l, device, reps=5):
+    """The mixed-precision workload (4 M points on the ellipsoid (1, 0.5, 0.25),
+    ell = 7, 1/r^4, SVD at eps = 1e-7), levels 4-6: every level in the low-rank
+    operators (FP64, FP32 on the CUDA cores) and in the full-rank ones (FP64, FP32,
+    TF32, BF16x3, TF32x3), timed per level with its lists classified once, and the
+    error of each against the FP64 full-rank result.  GFLOP/s counts the products
+    each one performs (full: 2 ell^6; low rank: 4 r_p ell^3 per interaction)."""
+    import numpy as np
+    import torch
+
+    from paper_1210_7292_gb300 import synth
+    ell, eps = 7, 1e-7
+    n3 = ell ** 3
+    pts, _ = synth.ellipsoid_surface(4_000_000, (1.0, 0.5, 0.25), seed=3)
+    ops = {"full": m2l.m2l_precompute(m2l.M2L_K_INV_R4, ell), "lowrank": m2l.m2l_precompute(m2l.M2L_K_INV_R4, ell, eps)}
+    ranks = m2l.m2l_ops_query(ops["lowrank"])[0]
+    out = {"workload": "4M points on the ellipsoid (1, 0.5, 0.25), ell 7, 1/r^4, SVD eps 1e-7",
+           "ranks": [int(r) for r in ranks], "levels": {}}
+    for L in (4, 5, 6):
+        cells = synth.occupied_cells(pts, L)
+        ijk = torch.from_numpy(cells).to(device)
+        off, src = m2l.m2l_build_lists(ijk, ijk)
+        lv = m2l.Level(2.0 / (1 << L), ijk, ijk, off, src, L)
+        plans = {k: m2l.m2l_plan_create(o, lv) for k, o in ops.items()}
+        counts, _ = m2l.m2l_plan_query(plans["full"])
+        w64 = torch.from_numpy(synth.gaussian_vectors(len(cells), n3, seed=33 + L)).to(device)
+        lr_flops = float(sum(4.0 * ranks[p] * n3 * counts[p] for p in range(16)))
+        full_flops = 2.0 * n3 * n3 * lv.nnz
+        res = {"cells": len(cells), "interactions": lv.nnz}
+        ref = None
+        for name, prec in (("full", "fp64"), ("lowrank", "fp64"), ("lowrank", "fp32"), ("full", "fp32"),
+                           ("full", "tf32"), ("full", "bf16x3"), ("full", "tf32x3")):
+            win = w64 if prec == "fp64" else w64.float()
+            loc = torch.zeros(len(cells), n3, dtype=torch.float64, device=device)
+            fp64_out = prec != "fp64"
+            m2l.m2l_plan_apply(plans[name], win, loc, prec, out_fp64=fp64_out)
+            torch.cuda.synchronize(device)
+            if ref is None:
+                ref = loc.clone()
+            err = float(torch.linalg.norm(loc - ref) / torch.linalg.norm(ref))
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                m2l.m2l_plan_apply(plans[name], win, loc, prec, out_fp64=fp64_out)
+                e1.record()
+                torch.cuda.synchronize(device)
+                ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            fl = full_flops if name == "full" else lr_flops
+            res["%s_%s" % (name, prec)] = {"ms": ms, "interactions_per_s": lv.nnz / (ms / 1e3),
+                                           "gflops": fl / (ms / 1e3) / 1e9, "rel_l2_vs_fp64_full": err}
+        for o in ops.values():
+            m2l.m2l_sync_status(o)
+        out["levels"][L] = res
+    return out
+
+
 def fmm_matvec(m2l, device, precision, reps=5):
     """The whole bbFMM matvec of the workload's particles on the GPU
     (m2l_fmm_evaluate: P2M, M2M, M2L at levels 2-5, L2L, L2P and near field);
@@ -693,6 +751,7 @@ def run_ours(args):
     pre = precompute_times(m2l, device) if (rank == 0 and not args.quick) else None
     variants = variants_compare(m2l, device, wl, flush) if (rank == 0 and not args.quick) else None
     dfmm = dfmm_m2l(m2l, device) if (rank == 0 and not args.quick) else None
+    cfg3 = config3_levels(m2l, device) if (rank == 0 and not args.quick) else None
     cpu = None
     if rank == 0 and world == 1 and not args.quick:
         cpu, ref_loc = cpu_oracle_sample(with_locals=True)
@@ -718,6 +777,7 @@ def run_ours(args):
                 "precompute": pre,
                 "variants": variants,
                 "dfmm_m2l": dfmm,
+                "config3": cfg3,
                 "clocks": clk,
                 "precisions": extra}
         print(json.dumps(line), flush=True)
