@@ -352,15 +352,20 @@ template <typename T> struct CT;
 template <> struct CT<float> { using V = float2; };
 template <> struct CT<double> { using V = double2; };
 
-// Tiles of NT interactions of one class: Bs [n3][NT + 1] gathered multipoles,
-// As [16][65] a slice of 64 operator rows (padded: the slice is written along
-// k), Cs [64][NT + 1] results.
-constexpr int kDLdA = 65;
+// Tiles of NT interactions of one class: Bs [kpad][NT + 1] gathered multipoles
+// (zero rows from n3 to kpad), As [16][MR + 1] a slice of MR = 64 operator
+// rows (padded: the slice is written along k), Cs [MR][NT + 1] results.
+// (A single 128-row pass for n3 <= 128 was slower: its register footprint
+// halves the resident blocks.)
+constexpr int kDRows = 64;
+
+__host__ __device__ __forceinline__ int d_kpad(int n3) { return (n3 + 15) / 16 * 16; }
 
 template <typename T>
 size_t d_apply_smem(int n3, int NT)
 {
-    return ((size_t)n3 * (NT + 1) + 16 * kDLdA + 64 * (NT + 1)) * sizeof(typename CT<T>::V);
+    const size_t b = (size_t)d_kpad(n3) * (NT + 1), a = (size_t)16 * (kDRows + 1), c = (size_t)kDRows * (NT + 1);
+    return (b + a + c) * sizeof(typename CT<T>::V);
 }
 
 template <typename T, int NT>
@@ -370,12 +375,14 @@ d_apply_kernel(int n3, int ntiles, const int4 *__restrict__ tiles, const int2 *_
                const int16_t *__restrict__ sinv, const typename CT<T>::V *__restrict__ W, T *__restrict__ F)
 {
     using V = typename CT<T>::V;
-    constexpr int NJ = NT / 16;
-    constexpr int LD = NT + 1;
+    constexpr int MR = kDRows;
+    constexpr int NJ = NT / 16, NI = MR / 16;
+    constexpr int LD = NT + 1, LDA = MR + 1;
     extern __shared__ __align__(16) unsigned char d_smem[];
+    const int kpad = d_kpad(n3);
     V *Bs = reinterpret_cast<V *>(d_smem);
-    V *As = Bs + (size_t)n3 * LD;
-    V *Cs = As + 16 * kDLdA;
+    V *As = Bs + (size_t)kpad * LD;
+    V *Cs = As + 16 * LDA;
     __shared__ int2 s_rec[NT];
     const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -397,17 +404,23 @@ d_apply_kernel(int n3, int ntiles, const int4 *__restrict__ tiles, const int2 *_
             }
             Bs[row * LD + j] = v;
         }
+        for (int idx = threadIdx.x; idx < (kpad - n3) * NT; idx += blockDim.x) {
+            V z;
+            z.x = T(0);
+            z.y = T(0);
+            Bs[(n3 + idx / NT) * LD + idx % NT] = z;
+        }
         __syncthreads();
         const V *Kp = K + (size_t)ti.x * n3 * n3;
-        for (int r0 = 0; r0 < n3; r0 += 64) {
-            T acc_re[4][NJ], acc_im[4][NJ];
+        for (int r0 = 0; r0 < n3; r0 += MR) {
+            T acc_re[NI][NJ], acc_im[NI][NJ];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < NI; ++i)
 #pragma unroll
                 for (int q = 0; q < NJ; ++q) acc_re[i][q] = acc_im[i][q] = T(0);
-            // the 64 x 16 operator slice: four elements per thread, the next slice
-            // loaded into registers while the current one is multiplied
-            constexpr int kPer = 64 * 16 / kDThreads;
+            // the MR x 16 operator slice, MR / 16 elements per thread; the next slice
+            // is loaded into registers while the current one is multiplied
+            constexpr int kPer = MR * 16 / kDThreads;
             V pre[kPer];
             auto load_slice = [&](int k0) {
 #pragma unroll
@@ -424,19 +437,19 @@ d_apply_kernel(int n3, int ntiles, const int4 *__restrict__ tiles, const int2 *_
 #pragma unroll
                 for (int u = 0; u < kPer; ++u) {
                     const int idx = threadIdx.x + u * kDThreads;
-                    As[(idx % 16) * kDLdA + idx / 16] = pre[u];
+                    As[(idx % 16) * LDA + idx / 16] = pre[u];
                 }
                 __syncthreads();
                 if (k0 + 16 < n3) load_slice(k0 + 16);
-                const int kmax = min(16, n3 - k0);
-                for (int kk = 0; kk < kmax; ++kk) {
-                    V a[4], b[NJ];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) a[i] = As[kk * kDLdA + tr + 16 * i];
+                for (int kk = 0; kk < 16; ++kk) {   // rows k0 + kk >= n3 of Bs hold zeros
+                    V a[NI], b[NJ];
+#pragma unroll
+                    for (int i = 0; i < NI; ++i) a[i] = As[kk * LDA + tr + 16 * i];
 #pragma unroll
                     for (int q = 0; q < NJ; ++q) b[q] = Bs[(k0 + kk) * LD + tc + 16 * q];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < NI; ++i)
 #pragma unroll
                         for (int q = 0; q < NJ; ++q) {
                             acc_re[i][q] += a[i].x * b[q].x - a[i].y * b[q].y;
@@ -446,7 +459,7 @@ d_apply_kernel(int n3, int ntiles, const int4 *__restrict__ tiles, const int2 *_
                 __syncthreads();
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < NI; ++i)
 #pragma unroll
                 for (int q = 0; q < NJ; ++q) {
                     V v;
@@ -456,8 +469,8 @@ d_apply_kernel(int n3, int ntiles, const int4 *__restrict__ tiles, const int2 *_
                 }
             __syncthreads();
             // row i of the class product is node sigma_g^-1(i) of the target
-            for (int idx = threadIdx.x; idx < 64 * NT; idx += blockDim.x) {
-                const int j = idx / 64, i = idx % 64;
+            for (int idx = threadIdx.x; idx < MR * NT; idx += blockDim.x) {
+                const int j = idx / MR, i = idx % MR;
                 if (j < ti.z && r0 + i < n3) {
                     const int2 r = s_rec[j];
                     const int a = sinv[rec_g(r.y) * n3 + r0 + i];
@@ -503,10 +516,11 @@ void dplan_release(m2l_dplan *p)
     delete p;
 }
 
+// Widest tile that fits shared memory.
 int pick_nt(int n3, size_t esz2)
 {
     for (int nt : {64, 32, 16}) {
-        const size_t smem = ((size_t)n3 * (nt + 1) + 16 * kDLdA + 64 * (nt + 1)) * esz2;
+        const size_t smem = ((size_t)d_kpad(n3) * (nt + 1) + 16 * (kDRows + 1) + kDRows * (nt + 1)) * esz2;
         if ((int)smem + 1024 <= max_smem_optin()) return nt;   // + the static tile records
     }
     return 0;
@@ -529,17 +543,28 @@ m2l_status d_launch(const m2l_dplan *p, const DevBuf &tiles, int ntiles, const v
 {
     using V = typename CT<T>::V;
     const size_t smem = d_apply_smem<T>(p->n3, NT);
-    M2L_CUDA(cudaFuncSetAttribute(d_apply_kernel<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kern = d_apply_kernel<T, NT>;
+    M2L_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    M2L_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, d_apply_kernel<T, NT>, kDThreads, smem));
+    M2L_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDThreads, smem));
     if (per_sm < 1) per_sm = 1;
     const int grid = (int)std::min<long>((long)num_sms() * per_sm, ntiles);
     const V *K = static_cast<const V *>(sizeof(T) == 8 ? p->K64.p : p->K32.p);
-    d_apply_kernel<T, NT><<<grid, kDThreads, smem, s>>>(p->n3, ntiles, tiles.as<int4>(), p->rec.as<int2>(), K,
-                                                         p->sigma.as<int16_t>(), p->sinv.as<int16_t>(),
-                                                         static_cast<const V *>(W), static_cast<T *>(F));
+    kern<<<grid, kDThreads, smem, s>>>(p->n3, ntiles, tiles.as<int4>(), p->rec.as<int2>(), K, p->sigma.as<int16_t>(),
+                                       p->sinv.as<int16_t>(), static_cast<const V *>(W), static_cast<T *>(F));
     M2L_LAUNCH_CHECK("d_apply_kernel");
     return M2L_OK;
+}
+
+template <typename T>
+m2l_status d_dispatch(const m2l_dplan *p, int nt, const DevBuf &tiles, int ntiles, const void *W, void *F,
+                      cudaStream_t s)
+{
+    if (nt == 64) return d_launch<T, 64>(p, tiles, ntiles, W, F, s);
+    if (nt == 32) return d_launch<T, 32>(p, tiles, ntiles, W, F, s);
+    if (nt == 16) return d_launch<T, 16>(p, tiles, ntiles, W, F, s);
+    set_error("order %d does not fit the directional apply's shared memory", p->ell);
+    return M2L_EUNSUPPORTED;
 }
 
 }  // namespace
@@ -784,19 +809,9 @@ m2l_status m2l_dfmm_plan_apply(const m2l_dplan *p, const void *multipoles, void 
     if (p->nnz == 0) return M2L_OK;
     if (!multipoles || !locals) { set_error("null multipoles or locals"); return M2L_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
-    if (precision == M2L_FP64) {
-        if (p->nt64 == 64) return d_launch<double, 64>(p, p->tiles64, p->ntiles64, multipoles, locals, s);
-        if (p->nt64 == 32) return d_launch<double, 32>(p, p->tiles64, p->ntiles64, multipoles, locals, s);
-        if (p->nt64 == 16) return d_launch<double, 16>(p, p->tiles64, p->ntiles64, multipoles, locals, s);
-    } else if (precision == M2L_FP32) {
-        if (p->nt32 == 64) return d_launch<float, 64>(p, p->tiles32, p->ntiles32, multipoles, locals, s);
-        if (p->nt32 == 32) return d_launch<float, 32>(p, p->tiles32, p->ntiles32, multipoles, locals, s);
-        if (p->nt32 == 16) return d_launch<float, 16>(p, p->tiles32, p->ntiles32, multipoles, locals, s);
-    } else {
-        set_error("the directional apply runs in M2L_FP64 or M2L_FP32");
-        return M2L_EUNSUPPORTED;
-    }
-    set_error("order %d does not fit the directional apply's shared memory", p->ell);
+    if (precision == M2L_FP64) return d_dispatch<double>(p, p->nt64, p->tiles64, p->ntiles64, multipoles, locals, s);
+    if (precision == M2L_FP32) return d_dispatch<float>(p, p->nt32, p->tiles32, p->ntiles32, multipoles, locals, s);
+    set_error("the directional apply runs in M2L_FP64 or M2L_FP32");
     return M2L_EUNSUPPORTED;
 }
 
