@@ -95,8 +95,11 @@ def _run(m2l, ell, k, level, cells, prec, seed=7):
 
 
 @pytest.mark.parametrize("ell,k,n,level", [(3, K_SPHERE, 30000, 4), (4, K_SPHERE, 20000, 5), (5, K_SPHERE, 8000, 3),
-                                           (4, 8.0, 3000, 5), (2, 8.0, 3000, 4)])
+                                           (4, 8.0, 3000, 5), (2, 8.0, 3000, 4), (6, 8.0, 3000, 4),
+                                           (7, K_SPHERE, 2000, 3), (8, 8.0, 1500, 3), (5, K_SPHERE, 20000, 7)])
 def test_apply_fp64_matches_oracle(m2l, ell, k, n, level):
+    """ell 6-8 take several 64-row blocks and narrower FP64 tiles; level 7 at
+    k = 32 (k w = 1/2) is low-frequency under a high-frequency parent."""
     cells = _cells(n, level)
     lv, W, F0, got = _run(m2l, ell, k, level, cells, "fp64")
     off, src = lv.il_offsets.cpu().numpy(), lv.il_sources.cpu().numpy()
@@ -112,11 +115,11 @@ def test_apply_fp64_matches_oracle(m2l, ell, k, n, level):
     assert np.array_equal(got[empty], F0[empty])
 
 
-@pytest.mark.parametrize("ell,level", [(5, 4), (4, 6)])
-def test_apply_fp32_matches_fp64(m2l, ell, level):
-    cells = _cells(30000, level)
-    _, _, F0, g64 = _run(m2l, ell, K_SPHERE, level, cells, "fp64")
-    _, _, _, g32 = _run(m2l, ell, K_SPHERE, level, cells, "fp32")
+@pytest.mark.parametrize("ell,level,k,n", [(5, 4, K_SPHERE, 30000), (4, 6, K_SPHERE, 30000), (8, 3, 8.0, 1500)])
+def test_apply_fp32_matches_fp64(m2l, ell, level, k, n):
+    cells = _cells(n, level)
+    _, _, F0, g64 = _run(m2l, ell, k, level, cells, "fp64")
+    _, _, _, g32 = _run(m2l, ell, k, level, cells, "fp32")
     err = oracle.rel_l2(g32 - F0, g64 - F0)
     print("dFMM fp32 vs fp64 ell=%d level=%d: %.2e" % (ell, level, err))
     assert err < 2e-6, err
