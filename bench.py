@@ -343,24 +343,35 @@ class Workload:
             cur.wait_event(done)
 
     def e2e_step(self):
-        """Same step through the public API from pinned host buffers: inputs copied in,
-        locals copied out, inside the timed region."""
+        """The same step through the public API from pinned host buffers: every level,
+        on its own stream, copies its inputs in, re-classifies its plan from the copied
+        lists, applies, and copies its locals out, all inside the timed region."""
         import torch
         m2l = self.m2l
+        cur = torch.cuda.current_stream(self.device)
+        m2l.m2l_ops_rebuild(self.ops, cur)
+        m2l.m2l_ops_prepare(self.ops, self.precision, cur)
+        ready = torch.cuda.Event()
+        ready.record(cur)
         dev_lv = {}
-        for L in LEVELS:
+        for L in sorted(LEVELS, reverse=True):   # the largest level first
+            s = self.streams[L]
+            s.wait_event(ready)
             h = self.host[L]
-            ijk = h["ijk"].to(self.device, non_blocking=True)
-            off = h["off"].to(self.device, non_blocking=True)
-            src = h["src"].to(self.device, non_blocking=True)
-            mp = h["mp"].to(self.device, non_blocking=True)
-            dev_lv[L] = (m2l.Level(2.0 / (1 << L), ijk, ijk, off, src, L), mp)
-        m2l.m2l_ops_rebuild(self.ops)
-        for L in LEVELS:
-            lv, mp = dev_lv[L]
-            loc = torch.zeros(lv.struct.ncells_tgt, ELL ** 3, dtype=self.dt_in, device=self.device)
-            m2l.m2l_apply_level(self.ops, lv, mp, loc, self.precision)
-            self.host[L]["loc"].copy_(loc, non_blocking=True)
+            with torch.cuda.stream(s):
+                ijk = h["ijk"].to(self.device, non_blocking=True)
+                off = h["off"].to(self.device, non_blocking=True)
+                src = h["src"].to(self.device, non_blocking=True)
+                mp = h["mp"].to(self.device, non_blocking=True)
+                lv = m2l.Level(2.0 / (1 << L), ijk, ijk, off, src, L)
+                loc = torch.zeros(lv.struct.ncells_tgt, ELL ** 3, dtype=self.dt_in, device=self.device)
+                m2l.m2l_plan_classify(self.plans[L], lv, s)
+                m2l.m2l_plan_apply(self.plans[L], mp, loc, self.precision, stream=s)
+                h["loc"].copy_(loc, non_blocking=True)
+            dev_lv[L] = (lv, mp, loc)
+            done = torch.cuda.Event()
+            done.record(s)
+            cur.wait_event(done)
         return dev_lv
 
     def e2e_bytes(self):
