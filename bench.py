@@ -567,7 +567,10 @@ def dfmm_m2l(m2l, device, reps=5):
            "levels": per_level, "interactions": total, "setup_ms": round(setup_ms, 1),
            "flop_convention": "8 ell^6 real flops per complex interaction"}
     res = {}
-    for prec, dt in (("fp64", torch.complex128), ("fp32", torch.complex64)):
+    for prec, dt in (("fp64", torch.complex128), ("fp32", torch.complex64), ("bf16x3", torch.complex64),
+                     ("tf32x3", torch.complex64), ("tf32", torch.complex64)):
+        for L in DFMM_LEVELS:   # tensor-core layouts are built ahead of the timing
+            m2l.m2l_dfmm_plan_prepare(plans[L], prec)
         W = {L: vecs[L].to(dt) for L in DFMM_LEVELS}
         F = {L: torch.zeros_like(W[L]) for L in DFMM_LEVELS}
 
@@ -587,9 +590,12 @@ def dfmm_m2l(m2l, device, reps=5):
             ts.append(e0.elapsed_time(e1))
         ms = statistics.median(ts)
         out[prec] = {"ms": ms, "interactions_per_s": total / (ms / 1e3), "tflops": flops / (ms / 1e3) / 1e12}
-    num = sum(float(torch.linalg.norm(res["fp32"][L] - res["fp64"][L]) ** 2) for L in DFMM_LEVELS)
+        for L in DFMM_LEVELS:
+            m2l.m2l_dfmm_plan_sync(plans[L])
     den = sum(float(torch.linalg.norm(res["fp64"][L]) ** 2) for L in DFMM_LEVELS)
-    out["fp32"]["rel_l2_vs_fp64"] = (num / den) ** 0.5
+    for prec in ("fp32", "bf16x3", "tf32x3", "tf32"):
+        num = sum(float(torch.linalg.norm(res[prec][L] - res["fp64"][L]) ** 2) for L in DFMM_LEVELS)
+        out[prec]["rel_l2_vs_fp64"] = (num / den) ** 0.5
     out["fp32"]["roofline"] = {"bound": "alu", "peak_tflops": round(FP32_ALU_TFLOPS, 1),
                                "frac": out["fp32"]["tflops"] / FP32_ALU_TFLOPS,
                                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (derived)"}
@@ -820,8 +826,8 @@ def run_apply_only(args):
 
 
 def run_dfmm_apply_only(args):
-    """The directional M2L of the dFMM workload's level 5 (ell = 5, FP32) alone,
-    three launches, for profiler captures of its apply kernel."""
+    """The directional M2L of the dFMM workload's level 5 (ell = 5) alone, three
+    launches in --dfmm-precision, for profiler captures of its apply kernel."""
     import torch
     import __graft_entry__ as g
     g.build()
@@ -833,15 +839,19 @@ def run_dfmm_apply_only(args):
     C, off, src = m2l.m2l_dfmm_build_lists(L, DFMM_K, ijk)
     plan = m2l.m2l_dfmm_plan_create(ELL, DFMM_K, m2l.DLevel(2.0 / (1 << L), ijk, ijk, C, off, src, L))
     n = ijk.shape[0] * C * ELL ** 3
-    W = torch.complex(torch.randn(n, device=device), torch.randn(n, device=device))
+    prec = args.dfmm_precision
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    W = torch.complex(torch.randn(n, device=device, dtype=dt), torch.randn(n, device=device, dtype=dt))
     F = torch.zeros_like(W)
+    m2l.m2l_dfmm_plan_prepare(plan, prec)
     for _ in range(3):
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record()
-        m2l.m2l_dfmm_plan_apply(plan, W, F, "fp32")
+        m2l.m2l_dfmm_plan_apply(plan, W, F, prec)
         e.record()
         torch.cuda.synchronize()
-        log("dFMM level-5 apply (fp32, %d interactions): %.3f ms" % (src.numel(), s.elapsed_time(e)))
+        log("dFMM level-5 apply (%s, %d interactions): %.3f ms" % (prec, src.numel(), s.elapsed_time(e)))
+    m2l.m2l_dfmm_plan_sync(plan)
     return 0
 
 
@@ -860,6 +870,8 @@ def main():
                     help="run three level-5 apply launches only (for profiler captures)")
     ap.add_argument("--dfmm-apply-only", action="store_true",
                     help="run three directional level-5 apply launches only (for profiler captures)")
+    ap.add_argument("--dfmm-precision", default="fp32", choices=["fp64", "fp32", "tf32", "bf16x3", "tf32x3"],
+                    help="precision of --dfmm-apply-only")
     args = ap.parse_args()
     args.compare = [p for p in args.compare.split(",") if p]
     if args.warmup < 3:

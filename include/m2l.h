@@ -387,10 +387,22 @@ void m2l_sa_free(m2l_sa *sa);
  *   M2L_EINVAL.
  * m2l_dfmm_plan_info: |T_sym|, n_cones, nnz; host_tsym [nsym][3] and
  *   host_np [nsym] when not NULL.
- * m2l_dfmm_plan_apply: locals += M2L(multipoles), stream-ordered, no
- *   allocation.  precision M2L_FP64 or M2L_FP32 (the product and the
- *   accumulation; results added with atomics, so the summation order of a
- *   target varies from run to run within rounding). */
+ * m2l_dfmm_plan_apply: locals += M2L(multipoles), stream-ordered.
+ *   M2L_FP64 / M2L_FP32: complex products on the CUDA cores (complex double /
+ *   complex float vectors).  M2L_TF32 / M2L_BF16X3 / M2L_TF32X3 (ell <= 5,
+ *   complex float vectors): the complex product as a real one of twice the
+ *   size, [[Re K, -Im K], [Im K, Re K]] on the stacked (Re, Im) vector, on
+ *   the tcgen05 tensor cores with FP32 accumulation.  Results are added with
+ *   atomics, so the summation order of a target varies from run to run
+ *   within rounding.  The first call in a tensor-core precision builds that
+ *   precision's operator images as m2l_dfmm_plan_prepare does (synchronous,
+ *   allocating); later calls allocate nothing.
+ * m2l_dfmm_plan_prepare: builds the layout of one precision ahead of the
+ *   first apply (synchronous).  M2L_EUNSUPPORTED for a tensor-core precision
+ *   with ell > 5.
+ * m2l_dfmm_plan_sync: synchronises `stream`, returns and clears the plan's
+ *   device status word (M2L_ETIMEOUT when a bounded wait of the tensor-core
+ *   kernel gave up). */
 typedef struct {
     int level;                   /* octree level, informational */
     double width;                /* cell width w (> 0) */
@@ -412,6 +424,8 @@ m2l_status m2l_dfmm_plan_info(const m2l_dplan *plan, int *nsym, int *n_cones, in
                               int64_t *host_np);
 m2l_status m2l_dfmm_plan_apply(const m2l_dplan *plan, const void *multipoles, void *locals, int precision,
                                void *stream);
+m2l_status m2l_dfmm_plan_prepare(m2l_dplan *plan, int precision, void *stream);
+m2l_status m2l_dfmm_plan_sync(const m2l_dplan *plan, void *stream);
 void m2l_dfmm_plan_free(m2l_dplan *plan);
 
 /* ---------------------------------------------------------------------

@@ -294,9 +294,9 @@ struct TileSched {
 // it starts at 0 and each caller asks for non-decreasing t, so the search
 // moves only at operator boundaries.
 __device__ __forceinline__ void tile_info(int t, const int *tile_start, const int *class_off, int NT, int &p,
-                                          int &col0, int &nc)
+                                          int &col0, int &nc, int last_cls = kNumSym - 1)
 {
-    while (p < 15 && t >= tile_start[p + 1]) ++p;
+    while (p < last_cls && t >= tile_start[p + 1]) ++p;
     col0 = class_off[p] + (t - tile_start[p]) * NT;
     nc = min(NT, class_off[p + 1] - col0);
 }
@@ -756,8 +756,11 @@ template <int KIND, int MT, int KA>
 __global__ void __launch_bounds__(kBigThreads, 1)
 tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, const uint8_t *__restrict__ a_img,
               const int16_t *__restrict__ sinv_pad, const float *__restrict__ mp, float *__restrict__ out_f32,
-              double *__restrict__ out_f64, int n3, float scale, int *status, int stall_first_stage)
+              double *__restrict__ out_f64, int n3, float scale, int *status, int stall_first_stage, int ncls,
+              const int *__restrict__ tile_start_g)
 {
+    // n3 is the vector length; with tile_start_g (device, ncls + 1 tile offsets)
+    // the classes are ncls operators of a_img, else the 16 of the symmetry method.
     using Tr = TcTraits<KIND>;
     using C = BigCfg<KIND, MT, KA>;
     constexpr int NT = kBigNT;
@@ -787,11 +790,15 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         int acc = 0;
-        for (int p = 0; p < 16; ++p) {
-            s_tile_start[p] = acc;
-            acc += (class_off[p + 1] - class_off[p] + NT - 1) / NT;
+        if (tile_start_g) {
+            acc = tile_start_g[ncls];
+        } else {
+            for (int p = 0; p < 16; ++p) {
+                s_tile_start[p] = acc;
+                acc += (class_off[p + 1] - class_off[p] + NT - 1) / NT;
+            }
+            s_tile_start[16] = acc;
         }
-        s_tile_start[16] = acc;
         const int per = (acc + gridDim.x - 1) / gridDim.x;
         s_sched.first = min(acc, (int)blockIdx.x * per);
         s_sched.last = min(acc, s_sched.first + per);
@@ -823,6 +830,8 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
     const uint32_t tmem_base = s_tmem_base;
     const int first = s_sched.first, last = s_sched.last;
     volatile int *abort_flag = &s_abort;
+    const int *ts = tile_start_g ? tile_start_g : s_tile_start;
+    const int lastc = (tile_start_g ? ncls : 16) - 1;
 
     if (warp < kProducerWarps) {
         // ------------------------------------------------------------ panel producers
@@ -831,7 +840,7 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
         for (int t = first; t < last; ++t) {
             const int i = t - first, s = i % NB, ks = i / NB;
             int col0, nc;
-            tile_info(t, s_tile_start, class_off, NT, p, col0, nc);
+            tile_info(t, ts, class_off, NT, p, col0, nc, lastc);
             int2 *prec = s_prec + s * NT;
             if (ptid < NT) prec[ptid] = (ptid < nc) ? __ldg(rec + col0 + ptid) : make_int2(0, 0);
             named_bar_sync(2, NPT);
@@ -959,7 +968,7 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
             for (int t = first; t < last; ++t) {
                 const int i = t - first;
                 int col0, nc;
-                tile_info(t, s_tile_start, class_off, NT, p, col0, nc);
+                tile_info(t, ts, class_off, NT, p, col0, nc, lastc);
                 bool ok = true;
                 for (int mt = 0; mt < MT && ok; ++mt)
                     for (int ka = 0; ka < KA; ++ka) {
@@ -990,7 +999,7 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
         for (int t = first; t < last; ++t) {
             const int i = t - first, buf = i & 1, kb = i >> 1;
             int col0, nc;
-            tile_info(t, s_tile_start, class_off, NT, p, col0, nc);
+            tile_info(t, ts, class_off, NT, p, col0, nc, lastc);
             if (a < NT) {
                 const int2 r = (a < nc) ? __ldg(rec + col0 + a) : make_int2(0, 0);
                 e_goff[a] = rec_g(r.y) * C::KPAD;
@@ -1274,7 +1283,8 @@ m2l_status launch_big(const m2l_ops *ops, const Buckets &b, Layout &L, const flo
     kern<<<(int)grid, kBigThreads, C::SMEM, s>>>(b.rec.as<int2>(), b.class_off.as<int>(), L.a.as<uint8_t>(),
                                                  L.b.as<int16_t>(), in, out_fp64 ? nullptr : (float *)out,
                                                  out_fp64 ? (double *)out : nullptr, n3, (float)scale, ops->d_status,
-                                                 (ops->debug_flags & M2L_DEBUG_STALL_PRODUCER) ? 1 : 0);
+                                                 (ops->debug_flags & M2L_DEBUG_STALL_PRODUCER) ? 1 : 0, kNumSym,
+                                                 nullptr);
     M2L_LAUNCH_CHECK("tc_big_kernel");
     return M2L_OK;
 }
@@ -1297,7 +1307,103 @@ m2l_status launch_big_ell(const m2l_ops *ops, const Buckets &b, Layout &L, const
     }
 }
 
+// The general form of the large-order kernel: ncls operator images of vector
+// length N <= 256 (one or two M tiles), tile offsets given on the device.
+template <int KIND, int MT, int KA>
+m2l_status launch_big_general(int N, int ncls, const int *tile_start, const int2 *rec, const int *class_off,
+                              const uint8_t *img, const int16_t *tinv, int nnz, const float *in, float *out,
+                              int *status, cudaStream_t s)
+{
+    using C = BigCfg<KIND, MT, KA>;
+    if (C::SMEM > max_smem_optin()) {
+        set_error("tensor-core kernel for vector length %d needs %d bytes of shared memory", N, C::SMEM);
+        return M2L_EUNSUPPORTED;
+    }
+    auto kern = tc_big_kernel<KIND, MT, KA>;
+    M2L_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    long grid = num_sms();
+    const long tiles_bound = (long)(nnz + kBigNT - 1) / kBigNT + ncls;
+    if (grid > tiles_bound) grid = tiles_bound;
+    kern<<<(int)grid, kBigThreads, C::SMEM, s>>>(rec, class_off, img, tinv, in, out, nullptr, N, 1.0f, status, 0, ncls,
+                                                 tile_start);
+    M2L_LAUNCH_CHECK("tc_big_kernel");
+    return M2L_OK;
+}
+
+template <int KIND>
+bool general_shape(int N, int &mt, int &ka)
+{
+    constexpr int E = 128 / TcTraits<KIND>::esz;
+    if (N <= 0 || N > 256) return false;
+    mt = N <= 128 ? 1 : 2;
+    ka = (mt * 128) / E;   // K padded to the M tiles
+    return true;
+}
+
 }  // namespace
+
+bool tc_general_config(int precision, int N, int *kpad, size_t *img_bytes_per_op)
+{
+    int mt = 0, ka = 0, esz = 0, nparts = 0;
+    switch (precision) {
+    case M2L_TF32: if (!general_shape<TC_TF32>(N, mt, ka)) return false; esz = 4; nparts = 1; break;
+    case M2L_BF16X3: if (!general_shape<TC_BF16X3>(N, mt, ka)) return false; esz = 2; nparts = 2; break;
+    case M2L_TF32X3: if (!general_shape<TC_TF32X3>(N, mt, ka)) return false; esz = 4; nparts = 2; break;
+    default: return false;
+    }
+    if (kpad) *kpad = ka * (128 / esz);
+    if (img_bytes_per_op) *img_bytes_per_op = (size_t)mt * ka * 128 * 128 * nparts;
+    return true;
+}
+
+m2l_status tc_general_images(int precision, int N, int ncls, const double *K, uint8_t *img, cudaStream_t s)
+{
+    int mt = 0, ka = 0;
+    dim3 grid(1, ncls);
+    switch (precision) {
+    case M2L_TF32:
+        general_shape<TC_TF32>(N, mt, ka);
+        grid.x = (unsigned)((mt * 128L * ka * 32 + 255) / 256);
+        a_block_image_kernel<TC_TF32><<<grid, 256, 0, s>>>(N, mt, ka, K, img);
+        break;
+    case M2L_BF16X3:
+        general_shape<TC_BF16X3>(N, mt, ka);
+        grid.x = (unsigned)((mt * 128L * ka * 64 + 255) / 256);
+        a_block_image_kernel<TC_BF16X3><<<grid, 256, 0, s>>>(N, mt, ka, K, img);
+        break;
+    case M2L_TF32X3:
+        general_shape<TC_TF32X3>(N, mt, ka);
+        grid.x = (unsigned)((mt * 128L * ka * 32 + 255) / 256);
+        a_block_image_kernel<TC_TF32X3><<<grid, 256, 0, s>>>(N, mt, ka, K, img);
+        break;
+    default:
+        set_error("not a tensor-core precision: %d", precision);
+        return M2L_EINVAL;
+    }
+    M2L_LAUNCH_CHECK("a_block_image_kernel");
+    return M2L_OK;
+}
+
+m2l_status tc_general_apply(int precision, int N, int ncls, const int *tile_start, const int2 *rec,
+                            const int *class_off, const uint8_t *img, const int16_t *tinv, int nnz, const float *in,
+                            float *out, int *status, cudaStream_t s)
+{
+    const bool two = N > 128;
+    switch (precision) {
+    case M2L_TF32:
+        return two ? launch_big_general<TC_TF32, 2, 8>(N, ncls, tile_start, rec, class_off, img, tinv, nnz, in, out, status, s)
+                   : launch_big_general<TC_TF32, 1, 4>(N, ncls, tile_start, rec, class_off, img, tinv, nnz, in, out, status, s);
+    case M2L_BF16X3:
+        return two ? launch_big_general<TC_BF16X3, 2, 4>(N, ncls, tile_start, rec, class_off, img, tinv, nnz, in, out, status, s)
+                   : launch_big_general<TC_BF16X3, 1, 2>(N, ncls, tile_start, rec, class_off, img, tinv, nnz, in, out, status, s);
+    case M2L_TF32X3:
+        return two ? launch_big_general<TC_TF32X3, 2, 8>(N, ncls, tile_start, rec, class_off, img, tinv, nnz, in, out, status, s)
+                   : launch_big_general<TC_TF32X3, 1, 4>(N, ncls, tile_start, rec, class_off, img, tinv, nnz, in, out, status, s);
+    default:
+        set_error("not a tensor-core precision: %d", precision);
+        return M2L_EINVAL;
+    }
+}
 
 m2l_status launch_tc(const m2l_ops *ops, const Buckets &b, const void *in, void *out, int precision, int out_fp64,
                      double scale, cudaStream_t s)

@@ -485,6 +485,39 @@ d_apply_kernel(int n3, int ntiles, const int4 *__restrict__ tiles, const int2 *_
     }
 }
 
+// The complex product as a real one of twice the size: rows and columns
+// [0, n3) hold real parts, [n3, 2 n3) imaginary parts,
+// Kr = [[Re K, -Im K], [Im K, Re K]] (row-major [nsym][2 n3][2 n3]).
+__global__ void d_embed_kernel(int n3, int nsym, const double2 *__restrict__ K, double *__restrict__ Kr)
+{
+    const int N = 2 * n3;
+    const long long total = (long long)nsym * N * N;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(idx / ((long long)N * N));
+        const int i = (int)((idx / N) % N), j = (int)(idx % N);
+        const double2 v = K[((size_t)p * n3 + i % n3) * n3 + j % n3];
+        double x;
+        if ((i < n3) == (j < n3)) x = v.x;
+        else x = (i < n3) ? -v.y : v.y;
+        Kr[idx] = x;
+    }
+}
+
+// tau_g^-1 over the stacked real vector, as indices into the interleaved complex
+// one: row k < n3 reads Re w[sigma_g^-1(k)] (2 s), row n3 + k reads its Im
+// (2 s + 1); padding rows read element 0 (their operator columns are zero).
+__global__ void d_tinv_kernel(int n3, int kpad, const int16_t *__restrict__ sinv, int16_t *__restrict__ tinv)
+{
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 48 * kpad; idx += gridDim.x * blockDim.x) {
+        const int g = idx / kpad, k = idx % kpad;
+        int v = 0;
+        if (k < n3) v = 2 * sinv[g * n3 + k];
+        else if (k < 2 * n3) v = 2 * sinv[g * n3 + k - n3] + 1;
+        tinv[idx] = (int16_t)v;
+    }
+}
+
 int d_grid(long n)
 {
     long b = (n + 255) / 256;
@@ -501,8 +534,12 @@ struct m2l_dplan {
     double k = 0.0, w = 0.0;
     std::vector<int32_t> tsym;       // [nsym][3], lexicographic
     std::vector<int64_t> np;         // interactions per class
-    m2l::DevBuf K64, K32, sigma, sinv, rec, tiles32, tiles64, status;
+    m2l::DevBuf K64, K32, sigma, sinv, rec, tiles32, tiles64, status, class_off;
     int ntiles32 = 0, ntiles64 = 0, nt32 = 64, nt64 = 32;
+    struct Tc {                      // tensor-core layout of one precision (built on first use)
+        m2l::DevBuf img, tinv, tstart;
+        bool ready = false;
+    } tc[3];                         // M2L_TF32, M2L_BF16X3, M2L_TF32X3
 };
 
 namespace {
@@ -511,7 +548,10 @@ void dplan_release(m2l_dplan *p)
 {
     if (!p) return;
     cudaDeviceSynchronize();
-    DevBuf *bs[] = {&p->K64, &p->K32, &p->sigma, &p->sinv, &p->rec, &p->tiles32, &p->tiles64, &p->status};
+    DevBuf *bs[] = {&p->K64,     &p->K32,        &p->sigma,      &p->sinv,      &p->rec,       &p->tiles32,
+                    &p->tiles64, &p->status,     &p->class_off,  &p->tc[0].img, &p->tc[0].tinv, &p->tc[0].tstart,
+                    &p->tc[1].img, &p->tc[1].tinv, &p->tc[1].tstart, &p->tc[2].img, &p->tc[2].tinv,
+                    &p->tc[2].tstart};
     for (DevBuf *b : bs) b->release();
     delete p;
 }
@@ -672,8 +712,9 @@ m2l_status m2l_dfmm_plan_create(int ell, double wavenumber, const m2l_dlevel *lv
     p->level = lv->level;
     p->k = wavenumber;
     p->w = lv->width;
-    DevBuf row_of, tmax, flags, pidx, code, cnt, cursor, coff, tsym;
-    ScratchGuard guard{&row_of, &tmax, &flags, &pidx, &code, &cnt, &cursor, &coff, &tsym};
+    DevBuf row_of, tmax, flags, pidx, code, cnt, cursor, tsym;
+    ScratchGuard guard{&row_of, &tmax, &flags, &pidx, &code, &cnt, &cursor, &tsym};
+    DevBuf &coff = p->class_off;
     m2l_status st = M2L_OK;
     auto fail = [&](m2l_status e) { dplan_release(p); return e; };
     const int nnz = lv->nnz, C = p->C, n3 = p->n3;
@@ -802,6 +843,57 @@ m2l_status m2l_dfmm_plan_info(const m2l_dplan *p, int *nsym, int *n_cones, int64
     return M2L_OK;
 }
 
+m2l_status m2l_dfmm_plan_prepare(m2l_dplan *p, int precision, void *stream)
+{
+    if (!p) { set_error("null directional plan"); return M2L_EINVAL; }
+    if (precision == M2L_FP64 || precision == M2L_FP32) return M2L_OK;
+    const int ti = precision == M2L_TF32 ? 0 : precision == M2L_BF16X3 ? 1 : precision == M2L_TF32X3 ? 2 : -1;
+    if (ti < 0) { set_error("unknown precision %d", precision); return M2L_EINVAL; }
+    m2l_dplan::Tc &L = p->tc[ti];
+    if (L.ready) return M2L_OK;
+    const int n3 = p->n3, N = 2 * n3, nsym = std::max(p->nsym, 1);
+    int kpad = 0;
+    size_t per_op = 0;
+    if (!tc_general_config(precision, N, &kpad, &per_op)) {
+        set_error("the directional tensor-core apply takes ell <= 5 (ell = %d)", p->ell);
+        return M2L_EUNSUPPORTED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    DevBuf Kr;
+    ScratchGuard guard{&Kr};
+    m2l_status st;
+    if ((st = Kr.ensure((size_t)nsym * N * N * sizeof(double))) != M2L_OK) return st;
+    if ((st = L.img.ensure((size_t)nsym * per_op)) != M2L_OK) return st;
+    if ((st = L.tinv.ensure((size_t)48 * kpad * sizeof(int16_t))) != M2L_OK) return st;
+    if ((st = L.tstart.ensure((size_t)(nsym + 1) * sizeof(int32_t))) != M2L_OK) return st;
+    if (p->nsym > 0) {
+        d_embed_kernel<<<d_grid((long)p->nsym * N * N), 256, 0, s>>>(n3, p->nsym, p->K64.as<double2>(), Kr.as<double>());
+        M2L_LAUNCH_CHECK("d_embed_kernel");
+        if ((st = tc_general_images(precision, N, p->nsym, Kr.as<double>(), L.img.as<uint8_t>(), s)) != M2L_OK)
+            return st;
+    }
+    d_tinv_kernel<<<d_grid(48L * kpad), 256, 0, s>>>(n3, kpad, p->sinv.as<int16_t>(), L.tinv.as<int16_t>());
+    M2L_LAUNCH_CHECK("d_tinv_kernel");
+    std::vector<int32_t> ts(p->nsym + 1, 0);   // tiles of 32 interactions per class
+    for (int q = 0; q < p->nsym; ++q) ts[q + 1] = ts[q] + (int)((p->np[q] + 31) / 32);
+    M2L_CUDA(cudaMemcpyAsync(L.tstart.p, ts.data(), ts.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    M2L_CUDA(cudaStreamSynchronize(s));
+    L.ready = true;
+    return M2L_OK;
+}
+
+m2l_status m2l_dfmm_plan_sync(const m2l_dplan *p, void *stream)
+{
+    if (!p) { set_error("null directional plan"); return M2L_EINVAL; }
+    M2L_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int st = 0;
+    M2L_CUDA(cudaMemcpy(&st, p->status.p, sizeof(int), cudaMemcpyDeviceToHost));
+    M2L_CUDA(cudaMemset(p->status.p, 0, sizeof(int)));
+    if (st & ST_TIMEOUT) { set_error("a bounded device wait timed out"); return M2L_ETIMEOUT; }
+    if (st) { set_error("directional apply status 0x%x", st); return M2L_EINVAL; }
+    return M2L_OK;
+}
+
 m2l_status m2l_dfmm_plan_apply(const m2l_dplan *p, const void *multipoles, void *locals, int precision,
                                void *stream)
 {
@@ -811,8 +903,17 @@ m2l_status m2l_dfmm_plan_apply(const m2l_dplan *p, const void *multipoles, void 
     cudaStream_t s = (cudaStream_t)stream;
     if (precision == M2L_FP64) return d_dispatch<double>(p, p->nt64, p->tiles64, p->ntiles64, multipoles, locals, s);
     if (precision == M2L_FP32) return d_dispatch<float>(p, p->nt32, p->tiles32, p->ntiles32, multipoles, locals, s);
-    set_error("the directional apply runs in M2L_FP64 or M2L_FP32");
-    return M2L_EUNSUPPORTED;
+    if (precision == M2L_TF32 || precision == M2L_BF16X3 || precision == M2L_TF32X3) {
+        m2l_status st = m2l_dfmm_plan_prepare(const_cast<m2l_dplan *>(p), precision, stream);
+        if (st != M2L_OK) return st;
+        const m2l_dplan::Tc &L = p->tc[precision == M2L_TF32 ? 0 : precision == M2L_BF16X3 ? 1 : 2];
+        return tc_general_apply(precision, 2 * p->n3, p->nsym, L.tstart.as<int>(), p->rec.as<int2>(),
+                                p->class_off.as<int>(), L.img.as<uint8_t>(), L.tinv.as<int16_t>(), p->nnz,
+                                static_cast<const float *>(multipoles), static_cast<float *>(locals),
+                                p->status.as<int>(), s);
+    }
+    set_error("unknown precision %d", precision);
+    return M2L_EINVAL;
 }
 
 void m2l_dfmm_plan_free(m2l_dplan *p) { dplan_release(p); }

@@ -96,6 +96,8 @@ def lib():
             "m2l_dfmm_plan_create": [I, D, ctypes.POINTER(m2l_dlevel), P, ctypes.POINTER(P)],
             "m2l_dfmm_plan_info": [P, P, P, P, P, P],
             "m2l_dfmm_plan_apply": [P, P, P, I, P],
+            "m2l_dfmm_plan_prepare": [P, I, P],
+            "m2l_dfmm_plan_sync": [P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -630,14 +632,22 @@ def m2l_dfmm_plan_info(plan: DPlan):
 
 def m2l_dfmm_plan_apply(plan: DPlan, multipoles, locals_, precision="fp32", stream=None):
     """locals_ += M2L(multipoles); complex tensors [ncells * n_cones, ell^3] (or
-    [ncells, n_cones, ell^3]), complex128 for "fp64", complex64 for "fp32"."""
+    [ncells, n_cones, ell^3]), complex128 for "fp64", complex64 for the others
+    ("fp32" on the CUDA cores; "tf32", "bf16x3", "tf32x3" on the tensor cores)."""
     import torch
     p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    dt = {M2L_FP64: torch.complex128, M2L_FP32: torch.complex64}.get(p)
-    if dt is None:
-        raise ValueError("the directional apply runs in fp64 or fp32")
+    dt = torch.complex128 if p == M2L_FP64 else torch.complex64
     for t, n, what in ((multipoles, plan.nsrc, "multipoles"), (locals_, plan.ntgt, "locals")):
         if t.numel() != n * plan.n_cones * plan.n3:
             raise ValueError("%s must hold %d x %d x %d values" % (what, n, plan.n_cones, plan.n3))
     _check("m2l_dfmm_plan_apply", lib().m2l_dfmm_plan_apply(plan.handle, _dev_ptr(multipoles, dt, "multipoles"),
                                                             _dev_ptr(locals_, dt, "locals"), p, _stream_ptr(stream)))
+
+
+def m2l_dfmm_plan_prepare(plan: DPlan, precision, stream=None):
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check("m2l_dfmm_plan_prepare", lib().m2l_dfmm_plan_prepare(plan.handle, p, _stream_ptr(stream)))
+
+
+def m2l_dfmm_plan_sync(plan: DPlan, stream=None):
+    _check("m2l_dfmm_plan_sync", lib().m2l_dfmm_plan_sync(plan.handle, _stream_ptr(stream)))

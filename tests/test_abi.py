@@ -73,6 +73,8 @@ def test_null_handles_rejected(lib):
     assert lib.m2l_dfmm_plan_create(4, 1.0, None, None, None) == m2l.M2L_EINVAL
     assert lib.m2l_dfmm_plan_info(None, None, None, None, None, None) == m2l.M2L_EINVAL
     assert lib.m2l_dfmm_plan_apply(None, None, None, 1, None) == m2l.M2L_EINVAL
+    assert lib.m2l_dfmm_plan_prepare(None, 3, None) == m2l.M2L_EINVAL
+    assert lib.m2l_dfmm_plan_sync(None, None) == m2l.M2L_EINVAL
     lib.m2l_dfmm_plan_free(None)
     assert lib.m2l_ops_aca_info(None, None, None) == m2l.M2L_EINVAL
     lib.m2l_fmm_free(None)

@@ -90,7 +90,7 @@ def _run(m2l, ell, k, level, cells, prec, seed=7):
     Wd = torch.from_numpy(W).to("cuda", dt)
     Fd = torch.from_numpy(F0).to("cuda", dt)
     m2l.m2l_dfmm_plan_apply(plan, Wd, Fd, prec)
-    torch.cuda.synchronize()
+    m2l.m2l_dfmm_plan_sync(plan)
     return lv, W, F0, Fd.to(torch.complex128).cpu().numpy()
 
 
@@ -160,3 +160,26 @@ def test_bad_lists_and_empty_level(m2l):
     z = torch.zeros((0, C0, 64), dtype=torch.complex64, device="cuda")
     m2l.m2l_dfmm_plan_apply(plan, z, z, "fp32")
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 2e-5), ("tf32x3", 2e-5), ("tf32", 2e-3)])
+@pytest.mark.parametrize("ell,level,k,n", [(5, 4, K_SPHERE, 30000), (4, 5, K_SPHERE, 30000), (3, 3, 8.0, 3000)])
+def test_apply_tensor_cores(m2l, prec, tol, ell, level, k, n):
+    """The complex product embedded as a real one on the tcgen05 kernel, against
+    the FP64 apply (BF16x3 and TF32x3 reach FP32-level error; TF32 does not)."""
+    cells = _cells(n, level)
+    lv, _, F0, g64 = _run(m2l, ell, k, level, cells, "fp64")
+    _, _, _, gtc = _run(m2l, ell, k, level, cells, prec)
+    err = oracle.rel_l2(gtc - F0, g64 - F0)
+    print("dFMM %s vs fp64 ell=%d level=%d: %.2e" % (prec, ell, level, err))
+    assert err < tol, err
+
+
+def test_tensor_cores_reject_large_orders(m2l):
+    cells = _cells(1500, 3)
+    ijk = torch.from_numpy(cells).cuda()
+    C, off, src = m2l.m2l_dfmm_build_lists(3, 8.0, ijk)
+    plan = m2l.m2l_dfmm_plan_create(6, 8.0, m2l.DLevel(d.level_width(3, 2.0), ijk, ijk, C, off, src, 3))
+    with pytest.raises(m2l.M2LError) as ei:
+        m2l.m2l_dfmm_plan_prepare(plan, "bf16x3")
+    assert ei.value.status == m2l.M2L_EUNSUPPORTED
