@@ -734,25 +734,25 @@ constexpr int kBigLoaderWarp = 9;
 constexpr int kBigEpiWarp0 = 10;
 constexpr int kBigThreads = 14 * 32;
 
-template <int KIND, int MT, int KA>
+template <int KIND, int MT, int KA, int NT_ = kBigNT>
 struct BigCfg {
     using Tr = TcTraits<KIND>;
     static constexpr int E = 128 / Tr::esz;                  // K elements per swizzle column
     static constexpr int KPAD = KA * E;
     static constexpr int A_BLOCK = 128 * 128 * Tr::nparts;   // one (M tile, K column) block, all parts
     static constexpr int A_PART = 128 * 128;
-    static constexpr int B_PART = KA * kBigNT * 128;
+    static constexpr int B_PART = KA * NT_ * 128;
     static constexpr int B_STAGE = B_PART * Tr::nparts;
     static constexpr int FS = MT * 128 + 4;                   // epilogue transpose column stride (floats)
-    static constexpr int FIXED = 1024 + 16 * FS * 4 + 2 * kBigNT * 8 + 2 * kBigNT * 4 + 32 * 8;
+    static constexpr int FIXED = 1024 + 16 * FS * 4 + 2 * NT_ * 8 + 2 * NT_ * 4 + 32 * 8;
     static constexpr int BUDGET = 225 * 1024;
     static constexpr int NB = (FIXED + 2 * B_STAGE + 3 * A_BLOCK <= BUDGET) ? 2 : 1;
     static constexpr int RS = (FIXED + NB * B_STAGE + 4 * A_BLOCK <= BUDGET) ? 4 : 3;
     static constexpr int SMEM = FIXED + NB * B_STAGE + RS * A_BLOCK;
-    static constexpr int TMEM_COLS = (2 * MT * kBigNT <= 128) ? 128 : ((2 * MT * kBigNT <= 256) ? 256 : 512);
+    static constexpr int TMEM_COLS = (2 * MT * NT_ <= 128) ? 128 : ((2 * MT * NT_ <= 256) ? 256 : 512);
 };
 
-template <int KIND, int MT, int KA>
+template <int KIND, int MT, int KA, int NT_ = kBigNT>
 __global__ void __launch_bounds__(kBigThreads, 1)
 tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, const uint8_t *__restrict__ a_img,
               const int16_t *__restrict__ sinv_pad, const float *__restrict__ mp, float *__restrict__ out_f32,
@@ -762,8 +762,8 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
     // n3 is the vector length; with tile_start_g (device, ncls + 1 tile offsets)
     // the classes are ncls operators of a_img, else the 16 of the symmetry method.
     using Tr = TcTraits<KIND>;
-    using C = BigCfg<KIND, MT, KA>;
-    constexpr int NT = kBigNT;
+    using C = BigCfg<KIND, MT, KA, NT_>;
+    constexpr int NT = NT_;
     constexpr int EPC = 16 / Tr::esz;
     constexpr int CPC = KA * 8;                      // 16-byte chunks per column and part
     constexpr int NPT = kProducerWarps * 32;
@@ -1309,20 +1309,28 @@ m2l_status launch_big_ell(const m2l_ops *ops, const Buckets &b, Layout &L, const
 
 // The general form of the large-order kernel: ncls operator images of vector
 // length N <= 256 (one or two M tiles), tile offsets given on the device.
+// Tiles hold 64 interactions where that fits shared memory (each operator block
+// streamed from L2 then serves twice the columns), else 32.
+template <int KIND, int MT, int KA>
+constexpr int general_nt()
+{
+    return BigCfg<KIND, MT, KA, 64>::SMEM <= 227 * 1024 ? 64 : kBigNT;
+}
 template <int KIND, int MT, int KA>
 m2l_status launch_big_general(int N, int ncls, const int *tile_start, const int2 *rec, const int *class_off,
                               const uint8_t *img, const int16_t *tinv, int nnz, const float *in, float *out,
                               int *status, cudaStream_t s)
 {
-    using C = BigCfg<KIND, MT, KA>;
+    constexpr int NT = general_nt<KIND, MT, KA>();
+    using C = BigCfg<KIND, MT, KA, NT>;
     if (C::SMEM > max_smem_optin()) {
         set_error("tensor-core kernel for vector length %d needs %d bytes of shared memory", N, C::SMEM);
         return M2L_EUNSUPPORTED;
     }
-    auto kern = tc_big_kernel<KIND, MT, KA>;
+    auto kern = tc_big_kernel<KIND, MT, KA, NT>;
     M2L_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
     long grid = num_sms();
-    const long tiles_bound = (long)(nnz + kBigNT - 1) / kBigNT + ncls;
+    const long tiles_bound = (long)(nnz + NT - 1) / NT + ncls;
     if (grid > tiles_bound) grid = tiles_bound;
     kern<<<(int)grid, kBigThreads, C::SMEM, s>>>(rec, class_off, img, tinv, in, out, nullptr, N, 1.0f, status, 0, ncls,
                                                  tile_start);
@@ -1342,15 +1350,29 @@ bool general_shape(int N, int &mt, int &ka)
 
 }  // namespace
 
-bool tc_general_config(int precision, int N, int *kpad, size_t *img_bytes_per_op)
+bool tc_general_config(int precision, int N, int *kpad, size_t *img_bytes_per_op, int *tile_cols)
 {
-    int mt = 0, ka = 0, esz = 0, nparts = 0;
+    int mt = 0, ka = 0, esz = 0, nparts = 0, nt = 0;
+    const bool two = N > 128;
     switch (precision) {
-    case M2L_TF32: if (!general_shape<TC_TF32>(N, mt, ka)) return false; esz = 4; nparts = 1; break;
-    case M2L_BF16X3: if (!general_shape<TC_BF16X3>(N, mt, ka)) return false; esz = 2; nparts = 2; break;
-    case M2L_TF32X3: if (!general_shape<TC_TF32X3>(N, mt, ka)) return false; esz = 4; nparts = 2; break;
+    case M2L_TF32:
+        if (!general_shape<TC_TF32>(N, mt, ka)) return false;
+        esz = 4; nparts = 1;
+        nt = two ? general_nt<TC_TF32, 2, 8>() : general_nt<TC_TF32, 1, 4>();
+        break;
+    case M2L_BF16X3:
+        if (!general_shape<TC_BF16X3>(N, mt, ka)) return false;
+        esz = 2; nparts = 2;
+        nt = two ? general_nt<TC_BF16X3, 2, 4>() : general_nt<TC_BF16X3, 1, 2>();
+        break;
+    case M2L_TF32X3:
+        if (!general_shape<TC_TF32X3>(N, mt, ka)) return false;
+        esz = 4; nparts = 2;
+        nt = two ? general_nt<TC_TF32X3, 2, 8>() : general_nt<TC_TF32X3, 1, 4>();
+        break;
     default: return false;
     }
+    if (tile_cols) *tile_cols = nt;
     if (kpad) *kpad = ka * (128 / esz);
     if (img_bytes_per_op) *img_bytes_per_op = (size_t)mt * ka * 128 * 128 * nparts;
     return true;

@@ -852,9 +852,9 @@ m2l_status m2l_dfmm_plan_prepare(m2l_dplan *p, int precision, void *stream)
     m2l_dplan::Tc &L = p->tc[ti];
     if (L.ready) return M2L_OK;
     const int n3 = p->n3, N = 2 * n3, nsym = std::max(p->nsym, 1);
-    int kpad = 0;
+    int kpad = 0, tcols = 0;
     size_t per_op = 0;
-    if (!tc_general_config(precision, N, &kpad, &per_op)) {
+    if (!tc_general_config(precision, N, &kpad, &per_op, &tcols)) {
         set_error("the directional tensor-core apply takes ell <= 5 (ell = %d)", p->ell);
         return M2L_EUNSUPPORTED;
     }
@@ -874,8 +874,8 @@ m2l_status m2l_dfmm_plan_prepare(m2l_dplan *p, int precision, void *stream)
     }
     d_tinv_kernel<<<d_grid(48L * kpad), 256, 0, s>>>(n3, kpad, p->sinv.as<int16_t>(), L.tinv.as<int16_t>());
     M2L_LAUNCH_CHECK("d_tinv_kernel");
-    std::vector<int32_t> ts(p->nsym + 1, 0);   // tiles of 32 interactions per class
-    for (int q = 0; q < p->nsym; ++q) ts[q + 1] = ts[q] + (int)((p->np[q] + 31) / 32);
+    std::vector<int32_t> ts(p->nsym + 1, 0);   // tiles of tcols interactions per class
+    for (int q = 0; q < p->nsym; ++q) ts[q + 1] = ts[q] + (int)((p->np[q] + tcols - 1) / tcols);
     M2L_CUDA(cudaMemcpyAsync(L.tstart.p, ts.data(), ts.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     M2L_CUDA(cudaStreamSynchronize(s));
     L.ready = true;

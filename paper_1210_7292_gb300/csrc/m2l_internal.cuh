@@ -168,10 +168,10 @@ int max_smem_optin();
 
 // General tensor-core apply (the large-order kernel over ncls operator images
 // of vector length N <= 256; used by the directional M2L).  tc_general_config
-// gives the padded K length of the inverse-permutation tables and the image
-// bytes per operator; tc_general_images builds the images from row-major FP64
+// gives the padded K length of the inverse-permutation tables, the image bytes
+// per operator and the interactions per tile; tc_general_images builds the images from row-major FP64
 // operators [ncls][N][N]; tc_general_apply adds into out.
-bool tc_general_config(int precision, int N, int *kpad, size_t *img_bytes_per_op);
+bool tc_general_config(int precision, int N, int *kpad, size_t *img_bytes_per_op, int *tile_cols);
 m2l_status tc_general_images(int precision, int N, int ncls, const double *K, uint8_t *img, cudaStream_t s);
 m2l_status tc_general_apply(int precision, int N, int ncls, const int *tile_start, const int2 *rec,
                             const int *class_off, const uint8_t *img, const int16_t *tinv, int nnz, const float *in,
