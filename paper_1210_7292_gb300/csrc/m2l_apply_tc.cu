@@ -734,7 +734,7 @@ constexpr int kBigLoaderWarp = 9;
 constexpr int kBigEpiWarp0 = 10;
 constexpr int kBigThreads = 14 * 32;
 
-template <int KIND, int MT, int KA, int NT_ = kBigNT>
+template <int KIND, int MT, int KA, int NT_ = kBigNT, int EG_ = 1>
 struct BigCfg {
     using Tr = TcTraits<KIND>;
     static constexpr int E = 128 / Tr::esz;                  // K elements per swizzle column
@@ -744,7 +744,7 @@ struct BigCfg {
     static constexpr int B_PART = KA * NT_ * 128;
     static constexpr int B_STAGE = B_PART * Tr::nparts;
     static constexpr int FS = MT * 128 + 4;                   // epilogue transpose column stride (floats)
-    static constexpr int FIXED = 1024 + 16 * FS * 4 + 2 * NT_ * 8 + 2 * NT_ * 4 + 32 * 8;
+    static constexpr int FIXED = 1024 + EG_ * 16 * FS * 4 + 2 * NT_ * 8 + EG_ * 2 * NT_ * 4 + 32 * 8;
     static constexpr int BUDGET = 225 * 1024;
     static constexpr int NB = (FIXED + 2 * B_STAGE + 3 * A_BLOCK <= BUDGET) ? 2 : 1;
     static constexpr int RS = (FIXED + NB * B_STAGE + 4 * A_BLOCK <= BUDGET) ? 4 : 3;
@@ -752,8 +752,12 @@ struct BigCfg {
     static constexpr int TMEM_COLS = (2 * MT * NT_ <= 128) ? 128 : ((2 * MT * NT_ <= 256) ? 256 : 512);
 };
 
-template <int KIND, int MT, int KA, int NT_ = kBigNT>
-__global__ void __launch_bounds__(kBigThreads, 1)
+// EG_ epilogue groups of four warps: with two, group g drains TMEM buffer g
+// (every other tile), each with its own transpose buffer and named barrier.
+constexpr int big_threads(int eg) { return (kBigEpiWarp0 + 4 * eg) * 32; }
+
+template <int KIND, int MT, int KA, int NT_ = kBigNT, int EG_ = 1>
+__global__ void __launch_bounds__(big_threads(EG_), 1)
 tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, const uint8_t *__restrict__ a_img,
               const int16_t *__restrict__ sinv_pad, const float *__restrict__ mp, float *__restrict__ out_f32,
               double *__restrict__ out_f64, int n3, float scale, int *status, int stall_first_stage, int ncls,
@@ -762,8 +766,9 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
     // n3 is the vector length; with tile_start_g (device, ncls + 1 tile offsets)
     // the classes are ncls operators of a_img, else the 16 of the symmetry method.
     using Tr = TcTraits<KIND>;
-    using C = BigCfg<KIND, MT, KA, NT_>;
+    using C = BigCfg<KIND, MT, KA, NT_, EG_>;
     constexpr int NT = NT_;
+    constexpr int EG = EG_;
     constexpr int EPC = 16 / Tr::esz;
     constexpr int CPC = KA * 8;                      // 16-byte chunks per column and part
     constexpr int NPT = kProducerWarps * 32;
@@ -775,11 +780,11 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
     uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint8_t *sRing = smem;                                        // RS operator blocks
     uint8_t *sB = sRing + RS * C::A_BLOCK;                        // NB panel stages
-    float *sF = reinterpret_cast<float *>(sB + NB * C::B_STAGE);   // [16][FS]
-    int2 *s_prec = reinterpret_cast<int2 *>(sF + 16 * FS);         // [NB][NT]
-    int *e_goff = reinterpret_cast<int *>(s_prec + 2 * NT);        // [NT]
-    int *e_tgt = e_goff + NT;                                      // [NT]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(e_tgt + NT);
+    float *sF_all = reinterpret_cast<float *>(sB + NB * C::B_STAGE);   // [EG][16][FS]
+    int2 *s_prec = reinterpret_cast<int2 *>(sF_all + EG * 16 * FS);    // [NB][NT]
+    int *e_goff_all = reinterpret_cast<int *>(s_prec + 2 * NT);        // [EG][NT]
+    int *e_tgt_all = e_goff_all + EG * NT;                             // [EG][NT]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(e_tgt_all + EG * NT);
     uint64_t *full = bars, *empty = bars + 2, *afull = bars + 4, *aempty = bars + 8, *tfull = bars + 12,
              *tempty = bars + 14, *drain = bars + 16;
     __shared__ uint32_t s_tmem_base;
@@ -989,8 +994,13 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue
-        const int a = threadIdx.x - kBigEpiWarp0 * 32;   // 0..127
+        const int grp = (threadIdx.x - kBigEpiWarp0 * 32) / 128;
+        const int a = threadIdx.x - kBigEpiWarp0 * 32 - 128 * grp;   // 0..127 within the group
         const int q = warp & 3;
+        const int bar_id = grp == 0 ? 1 : 3;
+        float *sF = sF_all + grp * 16 * FS;
+        int *e_goff = e_goff_all + grp * NT;
+        int *e_tgt = e_tgt_all + grp * NT;
         int cur = -1;
         float acc[MT];
 #pragma unroll
@@ -1000,13 +1010,14 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
             const int i = t - first, buf = i & 1, kb = i >> 1;
             int col0, nc;
             tile_info(t, ts, class_off, NT, p, col0, nc, lastc);
+            if (EG == 2 && buf != grp) continue;
             if (a < NT) {
                 const int2 r = (a < nc) ? __ldg(rec + col0 + a) : make_int2(0, 0);
                 e_goff[a] = rec_g(r.y) * C::KPAD;
                 e_tgt[a] = (a < nc) ? rec_tgt(r.y) : -1;
             }
             const bool ok = mbar_wait(tfull + buf, kb & 1, abort_flag, status);
-            if (named_bar_or(1, 128, ok ? 0 : 1)) break;
+            if (named_bar_or(bar_id, 128, ok ? 0 : 1)) break;
             tc_fence_after();
 #pragma unroll 1
             for (int ch = 0; ch < NT / 16; ++ch) {
@@ -1025,7 +1036,7 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
                             sF[jj * FS + __ldg(sinv_pad + e_goff[16 * ch + jj] + row)] = v[jj];
                     }
                 }
-                named_bar_sync(1, 128);
+                named_bar_sync(bar_id, 128);
                 int tg[16];
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) tg[jj] = e_tgt[16 * ch + jj];
@@ -1059,7 +1070,7 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
                         if (node < n3) acc[k] += sF[jj * FS + node];
                     }
                 }
-                named_bar_sync(1, 128);
+                named_bar_sync(bar_id, 128);
             }
         }
         if (cur >= 0) {
@@ -1311,10 +1322,12 @@ m2l_status launch_big_ell(const m2l_ops *ops, const Buckets &b, Layout &L, const
 // length N <= 256 (one or two M tiles), tile offsets given on the device.
 // Tiles hold 64 interactions where that fits shared memory (each operator block
 // streamed from L2 then serves twice the columns), else 32.
+constexpr int kGeneralEG = 2;
+
 template <int KIND, int MT, int KA>
 constexpr int general_nt()
 {
-    return BigCfg<KIND, MT, KA, 64>::SMEM <= 227 * 1024 ? 64 : kBigNT;
+    return BigCfg<KIND, MT, KA, 64, kGeneralEG>::SMEM <= 227 * 1024 ? 64 : kBigNT;
 }
 template <int KIND, int MT, int KA>
 m2l_status launch_big_general(int N, int ncls, const int *tile_start, const int2 *rec, const int *class_off,
@@ -1322,18 +1335,18 @@ m2l_status launch_big_general(int N, int ncls, const int *tile_start, const int2
                               int *status, cudaStream_t s)
 {
     constexpr int NT = general_nt<KIND, MT, KA>();
-    using C = BigCfg<KIND, MT, KA, NT>;
+    using C = BigCfg<KIND, MT, KA, NT, kGeneralEG>;
     if (C::SMEM > max_smem_optin()) {
         set_error("tensor-core kernel for vector length %d needs %d bytes of shared memory", N, C::SMEM);
         return M2L_EUNSUPPORTED;
     }
-    auto kern = tc_big_kernel<KIND, MT, KA, NT>;
+    auto kern = tc_big_kernel<KIND, MT, KA, NT, kGeneralEG>;
     M2L_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
     long grid = num_sms();
     const long tiles_bound = (long)(nnz + NT - 1) / NT + ncls;
     if (grid > tiles_bound) grid = tiles_bound;
-    kern<<<(int)grid, kBigThreads, C::SMEM, s>>>(rec, class_off, img, tinv, in, out, nullptr, N, 1.0f, status, 0, ncls,
-                                                 tile_start);
+    kern<<<(int)grid, big_threads(kGeneralEG), C::SMEM, s>>>(rec, class_off, img, tinv, in, out, nullptr, N, 1.0f,
+                                                             status, 0, ncls, tile_start);
     M2L_LAUNCH_CHECK("tc_big_kernel");
     return M2L_OK;
 }
