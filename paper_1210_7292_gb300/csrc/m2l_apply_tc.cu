@@ -732,7 +732,6 @@ tc_apply_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off,
 constexpr int kBigNT = 32;
 constexpr int kBigLoaderWarp = 9;
 constexpr int kBigEpiWarp0 = 10;
-constexpr int kBigThreads = 14 * 32;
 
 template <int KIND, int MT, int KA, int NT_ = kBigNT, int EG_ = 1>
 struct BigCfg {
@@ -1259,12 +1258,20 @@ __global__ void a_block_image_kernel(int n3, int MT, int KA, const double *__res
     }
 }
 
+// Two epilogue groups where their shared memory fits, else one.
+template <int KIND, int MT, int KA>
+constexpr int real_eg()
+{
+    return BigCfg<KIND, MT, KA, kBigNT, 2>::SMEM <= 227 * 1024 - 256 ? 2 : 1;
+}
+
 template <int KIND, int MT, int KA>
 m2l_status launch_big(const m2l_ops *ops, const Buckets &b, Layout &L, const float *in, void *out, int out_fp64,
                       double scale, cudaStream_t s)
 {
     using Tr = TcTraits<KIND>;
-    using C = BigCfg<KIND, MT, KA>;
+    constexpr int EG = real_eg<KIND, MT, KA>();
+    using C = BigCfg<KIND, MT, KA, kBigNT, EG>;
     const int n3 = ops->n3;
     const size_t img_bytes = (size_t)16 * MT * KA * C::A_BLOCK;
     m2l_status st;
@@ -1286,12 +1293,12 @@ m2l_status launch_big(const m2l_ops *ops, const Buckets &b, Layout &L, const flo
         set_error("tensor-core kernel for ell = %d needs %d bytes of shared memory", ops->ell, C::SMEM);
         return M2L_EUNSUPPORTED;
     }
-    auto kern = tc_big_kernel<KIND, MT, KA>;
+    auto kern = tc_big_kernel<KIND, MT, KA, kBigNT, EG>;
     M2L_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
     long grid = num_sms();
     const long tiles_bound = (long)(b.nnz + kBigNT - 1) / kBigNT + 16;
     if (grid > tiles_bound) grid = tiles_bound;
-    kern<<<(int)grid, kBigThreads, C::SMEM, s>>>(b.rec.as<int2>(), b.class_off.as<int>(), L.a.as<uint8_t>(),
+    kern<<<(int)grid, big_threads(EG), C::SMEM, s>>>(b.rec.as<int2>(), b.class_off.as<int>(), L.a.as<uint8_t>(),
                                                  L.b.as<int16_t>(), in, out_fp64 ? nullptr : (float *)out,
                                                  out_fp64 ? (double *)out : nullptr, n3, (float)scale, ops->d_status,
                                                  (ops->debug_flags & M2L_DEBUG_STALL_PRODUCER) ? 1 : 0, kNumSym,
