@@ -201,6 +201,7 @@ m2l_status lowrank_factors(m2l_ops *ops)
     const int n = ops->n3;
     const size_t nn = (size_t)n * n;
     DevBuf A, S, UM, VTM, work, info, dranks;
+    ScratchGuard guard{&A, &S, &UM, &VTM, &work, &info, &dranks};
     m2l_status st;
     if ((st = A.ensure(16 * nn * sizeof(double))) != M2L_OK) return st;
     if ((st = S.ensure(16 * (size_t)n * sizeof(double))) != M2L_OK) return st;
@@ -261,7 +262,6 @@ m2l_status lowrank_factors(m2l_ops *ops)
                                           VTM.as<double>(), ops->U64.as<double>(), ops->V64.as<double>());
     M2L_LAUNCH_CHECK("extract_lowrank_kernel");
     M2L_CUDA(cudaDeviceSynchronize());
-    A.release(); S.release(); UM.release(); VTM.release(); work.release(); info.release(); dranks.release();
     return M2L_OK;
 }
 
