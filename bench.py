@@ -514,8 +514,12 @@ def variants_compare(m2l, device, wl, flush, eps=1e-5, reps=5):
         sa = m2l.m2l_sa_create(wl.ops, eps, rc)
         setup = 1e3 * (time.perf_counter() - t0)
         r, nrc, _ = m2l.m2l_sa_info(sa)
-        run("sarcmp" if rc else "sa", lambda loc, sa=sa: m2l.m2l_sa_apply_level(sa, lv, mp32, loc, "fp32"),
+        name = "sarcmp" if rc else "sa"
+        run(name, lambda loc, sa=sa: m2l.m2l_sa_apply_level(sa, lv, mp32, loc, "fp32"),
             {"rank": r, "recompressed_cores": nrc, "setup_ms": round(setup, 1)})
+        # the cores on the tensor cores (dense C_t)
+        run(name + "_bf16x3", lambda loc, sa=sa: m2l.m2l_sa_apply_level(sa, lv, mp32, loc, "bf16x3"),
+            {"rank": r, "core": "tcgen05 BF16x3, dense C_t"})
         del sa
     t0 = time.perf_counter()
     ops_lr = m2l.m2l_precompute(m2l.M2L_K_INV_R, ELL, eps)

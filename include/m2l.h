@@ -328,10 +328,14 @@ void m2l_fmm_free(m2l_fmm *fmm);
  *   cores per transfer vector (f^[X] += C_t w^[Y]), decompress
  *   (F += scale U f^); scale as m2l_apply_level.  precision M2L_FP64 (double
  *   vectors) or M2L_FP32 (float multipoles; locals float, or double with
- *   locals_fp64 != 0).  Stream-ordered; allocates its workspace on first
- *   use or growth; list errors as m2l_apply_level (skipped entries, reported
- *   by m2l_sync_status on sa's ops).  Work on one m2l_sa object must be
- *   ordered on one stream.
+ *   locals_fp64 != 0) on the CUDA cores; M2L_TF32 / M2L_BF16X3 / M2L_TF32X3
+ *   (float vectors as M2L_FP32) run the cores on the tcgen05 tensor cores,
+ *   one class per transfer vector, with the dense C_t (X_t Y_t^T where SArcmp
+ *   recompressed it); the first call in such a precision builds its operator
+ *   images (synchronous, allocating).  Stream-ordered; allocates its
+ *   workspace on first use or growth; list errors as m2l_apply_level
+ *   (skipped entries, reported by m2l_sync_status on sa's ops).  Work on one
+ *   m2l_sa object must be ordered on one stream.
  * Errors: M2L_EINVAL (null or bad arguments), M2L_EUNSUPPORTED (rank,
  *   precision), M2L_ECUDA / M2L_ENOMEM. */
 typedef struct m2l_sa m2l_sa;

@@ -293,6 +293,50 @@ __global__ void sa_transpose_kernel(int r, const double *__restrict__ X, double 
     }
 }
 
+// Dense cores for the tensor-core apply: C_t itself, or X_t Y_t^T where SArcmp
+// recompressed it (the rank saving does not pay on the tensor cores).
+__global__ void sa_dense_kernel(int r, const int *__restrict__ kt, const double *__restrict__ X,
+                                const double *__restrict__ Y, double *__restrict__ Cd)
+{
+    const long long total = 343LL * r * r;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int sl = (int)(idx / ((long long)r * r));
+        const int a = (int)((idx / r) % r), b = (int)(idx % r);
+        const int k = kt[sl];
+        const double *Xs = X + (size_t)sl * r * r, *Ys = Y + (size_t)sl * r * r;
+        double v;
+        if (k == 0) {
+            v = Xs[(size_t)a * r + b];
+        } else {
+            v = 0.0;
+            for (int q = 0; q < k; ++q) v += Xs[(size_t)a * r + q] * Ys[(size_t)b * r + q];
+        }
+        Cd[idx] = v;
+    }
+}
+
+// Identity gather tables (no symmetry in SA): row k of the panel reads node k.
+__global__ void sa_identity_kernel(int r, int kpad, int16_t *__restrict__ tinv)
+{
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 48 * kpad; idx += gridDim.x * blockDim.x) {
+        const int k = idx % kpad;
+        tinv[idx] = (int16_t)(k < r ? k : 0);
+    }
+}
+
+// Tile offsets of the slot buckets for tiles of tcols interactions.
+__global__ void sa_tiles_kernel(const int32_t *__restrict__ start, int tcols, int32_t *__restrict__ tstart)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int acc = 0;
+    for (int sl = 0; sl < 343; ++sl) {
+        tstart[sl] = acc;
+        acc += (start[sl + 1] - start[sl] + tcols - 1) / tcols;
+    }
+    tstart[343] = acc;
+}
+
 int sa_grid(long n)
 {
     long b = (n + 255) / 256;
@@ -313,6 +357,12 @@ struct m2l_sa {
     m2l::DevBuf Xt64;                 // X transposed per slot (kernel layout)
     m2l::DevBuf U32t, B32, Xt32, Y32; // float copies for the FP32 apply
     m2l::DevBuf dkt, start, cursor, slot, rec, what, fhat, cnt;
+    struct Tc {                        // tensor-core images of the dense cores (built on first use)
+        m2l::DevBuf img, tinv;
+        int tcols = 0;
+        bool ready = false;
+    } tc[3];                           // M2L_TF32, M2L_BF16X3, M2L_TF32X3
+    m2l::DevBuf tstart;                // tile offsets per slot [344]
 };
 
 namespace {
@@ -321,8 +371,10 @@ void sa_release(m2l_sa *a)
 {
     if (!a) return;
     cudaDeviceSynchronize();
-    m2l::DevBuf *bs[] = {&a->U64t, &a->B64, &a->X64, &a->Y64, &a->Xt64, &a->U32t, &a->B32, &a->Xt32, &a->Y32,
-                         &a->dkt, &a->start, &a->cursor, &a->slot, &a->rec, &a->what, &a->fhat, &a->cnt};
+    m2l::DevBuf *bs[] = {&a->U64t,     &a->B64,       &a->X64,       &a->Y64,       &a->Xt64,      &a->U32t,
+                         &a->B32,      &a->Xt32,      &a->Y32,       &a->dkt,       &a->start,     &a->cursor,
+                         &a->slot,     &a->rec,       &a->what,      &a->fhat,      &a->cnt,       &a->tc[0].img,
+                         &a->tc[0].tinv, &a->tc[1].img, &a->tc[1].tinv, &a->tc[2].img, &a->tc[2].tinv, &a->tstart};
     for (m2l::DevBuf *b : bs) b->release();
     delete a;
 }
@@ -508,8 +560,39 @@ size_t sa_core_smem(int r, size_t esz, bool stage)
     return (size_t)(2 * kSaTile * r + (stage ? r * r + r * (r / 2) : 0)) * esz;
 }
 
+m2l_status sa_prepare_tc(m2l_sa *a, int precision, cudaStream_t s)
+{
+    const int ti = precision == M2L_TF32 ? 0 : precision == M2L_BF16X3 ? 1 : 2;
+    m2l_sa::Tc &L = a->tc[ti];
+    if (L.ready) return M2L_OK;
+    const int r = a->r;
+    int kpad = 0, tcols = 0;
+    size_t per_op = 0;
+    if (!tc_general_config(precision, r, &kpad, &per_op, &tcols)) {
+        set_error("no tensor-core configuration for SA rank %d", r);
+        return M2L_EUNSUPPORTED;
+    }
+    DevBuf Cd;
+    ScratchGuard guard{&Cd};
+    SA_TRY(Cd.ensure(343ULL * r * r * sizeof(double)));
+    SA_TRY(L.img.ensure(343ULL * per_op));
+    SA_TRY(L.tinv.ensure((size_t)48 * kpad * sizeof(int16_t)));
+    SA_TRY(a->tstart.ensure(344 * sizeof(int32_t)));
+    sa_dense_kernel<<<sa_grid(343L * r * r), 256, 0, s>>>(r, a->dkt.as<int>(), a->X64.as<double>(), a->Y64.as<double>(),
+                                                          Cd.as<double>());
+    M2L_LAUNCH_CHECK("sa_dense_kernel");
+    SA_TRY(tc_general_images(precision, r, 343, Cd.as<double>(), L.img.as<uint8_t>(), s));
+    sa_identity_kernel<<<sa_grid(48L * kpad), 256, 0, s>>>(r, kpad, L.tinv.as<int16_t>());
+    M2L_LAUNCH_CHECK("sa_identity_kernel");
+    M2L_CUDA(cudaStreamSynchronize(s));
+    L.tcols = tcols;
+    L.ready = true;
+    return M2L_OK;
+}
+
 template <typename T, typename TO>
-m2l_status sa_apply(m2l_sa *a, const m2l_level *lv, const T *w, TO *loc, double scale, cudaStream_t s)
+m2l_status sa_apply(m2l_sa *a, const m2l_level *lv, const T *w, TO *loc, double scale, cudaStream_t s,
+                    int tc_precision = -1)
 {
     const int r = a->r, n3 = a->n3, nnz = lv->nnz;
     const int ntgt = lv->ncells_tgt, nsrc = lv->ncells_src;
@@ -542,6 +625,19 @@ m2l_status sa_apply(m2l_sa *a, const m2l_level *lv, const T *w, TO *loc, double 
     }
     // core: f^[X] += C_t w^[Y]
     M2L_CUDA(cudaMemsetAsync(a->fhat.p, 0, (size_t)ntgt * r * sizeof(T), s));
+    if constexpr (sizeof(T) == 4) {
+        if (tc_precision >= 0) {   // on the tensor cores, one class per transfer vector
+            const m2l_sa::Tc &L = a->tc[tc_precision == M2L_TF32 ? 0 : tc_precision == M2L_BF16X3 ? 1 : 2];
+            sa_tiles_kernel<<<1, 32, 0, s>>>(a->start.as<int32_t>(), L.tcols, a->tstart.as<int32_t>());
+            M2L_LAUNCH_CHECK("sa_tiles_kernel");
+            SA_TRY(tc_general_apply(tc_precision, r, 343, a->tstart.as<int>(), a->rec.as<int2>(), a->start.as<int>(),
+                                    L.img.as<uint8_t>(), L.tinv.as<int16_t>(), nnz, a->what.as<float>(),
+                                    a->fhat.as<float>(), a->ops->d_status, s));
+            gemm_rm<T, TO, true>(ntgt, n3, r, a->fhat.as<T>(), r, 0, Ut, n3, 0, loc, n3, 0, 1, scale, s);
+            M2L_LAUNCH_CHECK("gemm(decompress)");
+            return M2L_OK;
+        }
+    }
     const bool stage = (int)sa_core_smem(r, sizeof(T), true) + 4096 <= max_smem_optin();
     const size_t smem = sa_core_smem(r, sizeof(T), stage);
     const long tiles_bound = (long)nnz / kSaTile + 343;
@@ -626,8 +722,15 @@ m2l_status m2l_sa_apply_level(const m2l_sa *sa_c, const m2l_level *level, const 
         if (locals_fp64) return sa_apply<float, double>(sa, level, (const float *)multipoles, (double *)locals, scale, s);
         return sa_apply<float, float>(sa, level, (const float *)multipoles, (float *)locals, scale, s);
     }
-    set_error("the SA apply runs in M2L_FP64 or M2L_FP32");
-    return M2L_EUNSUPPORTED;
+    if (precision == M2L_TF32 || precision == M2L_BF16X3 || precision == M2L_TF32X3) {
+        m2l_status st = sa_prepare_tc(sa, precision, s);
+        if (st != M2L_OK) return st;
+        if (locals_fp64)
+            return sa_apply<float, double>(sa, level, (const float *)multipoles, (double *)locals, scale, s, precision);
+        return sa_apply<float, float>(sa, level, (const float *)multipoles, (float *)locals, scale, s, precision);
+    }
+    set_error("unknown precision %d", precision);
+    return M2L_EINVAL;
 }
 
 void m2l_sa_free(m2l_sa *sa) { sa_release(sa); }

@@ -148,3 +148,13 @@ def test_sa_bad_list_and_empty_level(m2l):
     with pytest.raises(m2l.M2LError) as ei:
         m2l.m2l_sa_create(ops, 1.5)
     assert ei.value.status == m2l.M2L_EINVAL
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 2e-5), ("tf32x3", 2e-5), ("tf32", 2e-3)])
+@pytest.mark.parametrize("ell,kind,eps,rcmp", [(5, 0, 1e-5, False), (5, 1, 1e-6, True), (4, 2, 1e-5, True)])
+def test_sa_apply_tensor_cores(m2l, ell, kind, eps, rcmp, prec, tol):
+    """The cores on the tcgen05 kernel (one class per transfer vector) against the
+    oracle's SA operators; BF16x3 and TF32x3 reach FP32-level error."""
+    err, _, _ = _apply_case(m2l, ell, kind, eps, rcmp, 4, 0.25, 6, prec, True)
+    print("SA apply %s ell=%d kind=%d eps=%g rcmp=%d: rel L2 %.2e" % (prec, ell, kind, eps, rcmp, err))
+    assert err < tol, err
