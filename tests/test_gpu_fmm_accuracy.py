@@ -13,6 +13,7 @@ level and that the FP32-accurate precisions meet the criterion.
 """
 import json
 import os
+import tempfile
 
 import numpy as np
 import pytest
@@ -23,8 +24,8 @@ from gpu_helpers import device
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-RESULT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out",
-                      "fmm_accuracy_config2.json")
+# the per-precision errors are written as JSON to M2L_RESULTS_DIR (default: the system temp dir)
+RESULT = os.path.join(os.environ.get("M2L_RESULTS_DIR", tempfile.gettempdir()), "fmm_accuracy_config2.json")
 
 
 @pytest.fixture(scope="module")
