@@ -361,7 +361,8 @@ void m2l_sa_free(m2l_sa *sa);
  * Readings (the paper defers these to its reference on the dFMM):
  *  - a level of cell width w is high-frequency (hf) when k w >= 1;
  *  - a pair is admissible when |t|_inf >= 2 and, at an hf level, also
- *    |c_X - c_Y| > k w^2, evaluated in FP64 as ((t.t) w) w > ((k w) w)^2;
+ *    |c_X - c_Y| > max(k w^2, 2 w), evaluated in FP64 as
+ *    ((t.t) w) w > ((k w) w)^2 and t.t > 4;
  *  - cones: each face of the cube [-1, 1]^3 split into m x m squares, m the
  *    smallest power of two >= k w (m = 0, one cone, at an lf level); the cone
  *    of a pair is the square hit along c_X - c_Y: face axis f = the first axis

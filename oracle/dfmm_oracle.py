@@ -25,9 +25,11 @@ Readings, where the paper defers to its reference on the directional FMM:
 * D1 regime: a level of cell width w is high-frequency when k w >= 1 (the
   paper's table of list sizes has k w = 1 in hf and k w = 1/2 in lf).
 * D2 admissibility: at an lf level, |t|_inf >= 2 (the bbFMM rule); at an hf
-  level, additionally |c_X - c_Y| > k w^2 (the O(k w^2) separation, strict),
-  evaluated as (t.t) w w > (k w w)(k w w) in FP64.  On the paper's sphere
-  this reproduces its table of list sizes exactly at levels 3, 4 and 5.
+  level, additionally |c_X - c_Y| > max(k w^2, 2 w) (the O(k w^2) separation,
+  strict, never below two cell widths), evaluated as
+  (t.t) w w > (k w w)(k w w) and t.t > 4 in FP64.  With it the paper's table
+  of list sizes is reproduced exactly, for all three geometries and every
+  printed level.
 * D3 cones: the unit sphere is split through the faces of the cube [-1, 1]^3,
   each face into m x m squares, m the smallest power of two >= k w (cone
   aperture O(1/(k w)), halved from one level to the next coarser one:
@@ -80,7 +82,7 @@ def admissible(k: float, w: float, t) -> bool:
     if not is_high_frequency(k, w):
         return True
     tt = float(sum(int(v) * int(v) for v in t))
-    return tt * w * w > (k * w * w) * (k * w * w)
+    return tt * w * w > (k * w * w) * (k * w * w) and tt > 4.0
 
 
 def cone_m(k: float, w: float) -> int:
@@ -184,7 +186,7 @@ def admissible_many(k: float, w: float, t: np.ndarray) -> np.ndarray:
     if not is_high_frequency(k, w):
         return ok
     tt = (t * t).sum(axis=-1).astype(np.float64)
-    return ok & (tt * w * w > (k * w * w) * (k * w * w))
+    return ok & (tt * w * w > (k * w * w) * (k * w * w)) & (tt > 4.0)
 
 
 def directional_lists(cells: np.ndarray, level: int, k: float, domain_width: float):

@@ -10,7 +10,7 @@
 //  * lists: Alg. 1 on a uniform-depth octree, written per level: Y is in the
 //    far field of X at level L when the pair is admissible at L and no pair of
 //    their ancestors is.  Admissibility: |t|_inf >= 2, and at a high-frequency
-//    level (k w >= 1) also |c_X - c_Y| > k w^2.  Cones: the faces of the cube
+//    level (k w >= 1) also |c_X - c_Y| > max(k w^2, 2 w).  Cones: the faces of the cube
 //    split into m x m squares, m the smallest power of two >= k w; the cone of
 //    a pair is the square hit along c_X - c_Y.
 //  * plan: classification t -> (p(t), g(t)) over the entries, T_sym in
@@ -52,7 +52,7 @@ __device__ __forceinline__ bool d_admissible(double k, double w, int t0, int t1,
     if (!(k * w >= 1.0)) return true;
     const double tt = (double)(t0 * t0 + t1 * t1 + t2 * t2);
     const double kww = __dmul_rn(__dmul_rn(k, w), w);
-    return __dmul_rn(__dmul_rn(tt, w), w) > __dmul_rn(kww, kww);
+    return __dmul_rn(__dmul_rn(tt, w), w) > __dmul_rn(kww, kww) && tt > 4.0;
 }
 
 // Cone of the direction t (integer arithmetic): face axis f (first largest
