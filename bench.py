@@ -332,8 +332,11 @@ class Workload:
         for L in sorted(LEVELS, reverse=True):   # the largest level first: it is the critical path
             s = self.streams[L]
             s.wait_event(ready)
+            if kev is not None:
+                kev[L][2].record(s)
             m2l.m2l_plan_classify(self.plans[L], self.levels[L], s)
             if kev is not None:
+                kev[L][3].record(s)
                 kev[L][0].record(s)
             m2l.m2l_plan_apply(self.plans[L], self.mp[L], self.loc[L], self.precision, stream=s)
             if kev is not None:
@@ -386,7 +389,8 @@ class Workload:
 def timed(fn, steps, flush, device, kernel_events=False, levels=LEVELS):
     import torch
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    kev = [{L: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for L in levels}
+    # per level: apply start/end, classification start/end
+    kev = [{L: tuple(torch.cuda.Event(enable_timing=True) for _ in range(4)) for L in levels}
            for _ in range(steps)] if kernel_events else None
     for i in range(steps):
         flush.zero_()   # evict L2 between timed steps (outside the event pair)
@@ -401,6 +405,7 @@ def timed(fn, steps, flush, device, kernel_events=False, levels=LEVELS):
     kt = None
     if kernel_events:
         kt = {L: [k[L][0].elapsed_time(k[L][1]) / 1e3 for k in kev] for L in levels}
+        kt["classify"] = {L: [k[L][2].elapsed_time(k[L][3]) / 1e3 for k in kev] for L in levels}
     return total, kt
 
 
@@ -789,6 +794,11 @@ def run_ours(args):
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "gflops": value * FLOPS_PER_INTERACTION / 1e9,
                 "level5_kernel_ms": 1e3 * k5,
+                "per_level": {L: {"interactions": wl.nint[L], "apply_ms": 1e3 * statistics.mean(kt[L]),
+                                  "classify_ms": 1e3 * statistics.mean(kt["classify"][L]),
+                                  "interactions_per_s": wl.nint[L] / statistics.mean(kt[L]),
+                                  "gflops": FLOPS_PER_INTERACTION * wl.nint[L] / statistics.mean(kt[L]) / 1e9}
+                              for L in LEVELS},
                 "roofline": roofline(prec, ach, peaks, src_kind),
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": "interactions/s", "h2d_bytes_per_step": h2d,
