@@ -39,8 +39,6 @@ WORKLOAD = ("uniform octree of [-1,1]^3, N=2,000,000 particles U([-1,1]^3), leaf
 METRIC = "M2L interactions/s (levels 2-5, one pass of the hot path)"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 NOMINAL = {"bf16": 2250.0, "tf32": 1100.0}
-# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
-FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FLOPS_PER_INTERACTION = 2 * (ELL ** 3) ** 2
 
 
@@ -433,20 +431,56 @@ KERNEL_FOR = {"fp64": ("simt_apply_kernel<double>", "m2l_apply_simt.cu", "alu"),
               "tf32x3": ("tc_apply_kernel<tf32x3>", "m2l_apply_tc.cu", "tensor")}
 
 
-def roofline(precision, achieved_tflops, peaks, src_kind):
+def matmul_peaks(device, n=8192):
+    """Dense matrix-product throughput of this GPU, measured here with
+    torch.matmul (cuBLAS) on n x n x n products, best of a few: FP64, FP32 with
+    TF32 off, and TF32.  These are the roofline denominators of the FP64, FP32
+    and TF32 kernels (the BF16 peaks come from MEASURED_PEAKS.json)."""
+    import torch
+    keep = torch.backends.cuda.matmul.allow_tf32
+    out = {}
+    try:
+        for name, dt, tf32, reps in (("fp64", torch.float64, False, 3), ("fp32", torch.float32, False, 5),
+                                     ("tf32", torch.float32, True, 10)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            g = torch.Generator(device=device).manual_seed(1)
+            a = torch.randn(n, n, device=device, dtype=dt, generator=g)
+            b = torch.randn(n, n, device=device, dtype=dt, generator=g)
+            c = torch.matmul(a, b)
+            torch.cuda.synchronize(device)
+            best = float("inf")
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                torch.cuda.synchronize(device)
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+            out[name] = 2.0 * n ** 3 / best / 1e12
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = keep
+    out["how"] = "torch.matmul %d^3, best of 3 (fp64) / 5 (fp32, TF32 off) / 10 (tf32), this run" % n
+    return out
+
+
+def roofline(precision, achieved_tflops, peaks, src_kind, mm):
+    """Roofline of the level-5 apply kernel.  The kernel is timed per launch
+    inside a step of about a millisecond, so the BF16 denominator is the burst
+    peak; the split precisions execute three tensor products per algorithmic
+    one, so their peak is the product peak / 3."""
     kname, src, bound = KERNEL_FOR[precision]
+    bf = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])
     if precision == "fp32":
-        peak, how = FP32_ALU_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
+        peak, how = mm["fp32"], "FP32 matmul (TF32 off) measured in this run"
     elif precision == "fp64":
-        peak, how = 1.25, "nominal FP64 1.25 TFLOP/s (no measured FP64 peak in MEASURED_PEAKS)"
+        peak, how = mm["fp64"], "FP64 matmul measured in this run"
+    elif precision == "tf32":
+        peak, how = mm["tf32"], "TF32 matmul measured in this run"
+    elif precision == "bf16x3":
+        peak, how = bf / 3.0, "bf16 burst (%s, MEASURED_PEAKS.json) / 3 products" % src_kind
     else:
-        bf = peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"])
-        if precision == "tf32":
-            peak, how = bf * NOMINAL["tf32"] / NOMINAL["bf16"], "bf16 sustained (%s) x 1.1/2.25" % src_kind
-        elif precision == "bf16x3":
-            peak, how = bf / 3.0, "bf16 sustained (%s) / 3 products" % src_kind
-        else:
-            peak, how = bf * NOMINAL["tf32"] / NOMINAL["bf16"] / 3.0, "bf16 sustained (%s) x 1.1/2.25 / 3" % src_kind
+        peak, how = mm["tf32"] / 3.0, "TF32 matmul measured in this run / 3 products"
     nprod = 3 if precision in ("bf16x3", "tf32x3") else 1   # tensor products per algorithmic one
     return {"bound": bound, "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved_tflops / peak, "traffic": traffic_for(kname), "kernel": kname, "peak_source": how,
@@ -540,10 +574,9 @@ def variants_compare(m2l, device, wl, flush, eps=1e-5, reps=5):
 DFMM_PARTICLES = 168931   # the paper's sphere (Sec. 5)
 DFMM_K = 32.0             # k = 1 in its box of side 64, on the unit domain of side 2
 DFMM_LEVELS = (3, 4, 5, 6)
-FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 
-def dfmm_m2l(m2l, device, reps=5):
+def dfmm_m2l(m2l, device, mm, reps=5):
     """The directional (Helmholtz) M2L of the paper's sphere at ell = 5 over its
     high-frequency levels 3-6: lists and plans built once (set-up, timed apart),
     then every level's complex M2L per pass, FP32 and FP64 (the FP32 error
@@ -605,9 +638,9 @@ def dfmm_m2l(m2l, device, reps=5):
     for prec in ("fp32", "bf16x3", "tf32x3", "tf32"):
         num = sum(float(torch.linalg.norm(res[prec][L] - res["fp64"][L]) ** 2) for L in DFMM_LEVELS)
         out[prec]["rel_l2_vs_fp64"] = (num / den) ** 0.5
-    out["fp32"]["roofline"] = {"bound": "alu", "peak_tflops": round(FP32_ALU_TFLOPS, 1),
-                               "frac": out["fp32"]["tflops"] / FP32_ALU_TFLOPS,
-                               "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (derived)"}
+    out["fp32"]["roofline"] = {"bound": "alu", "peak_tflops": round(mm["fp32"], 1),
+                               "frac": out["fp32"]["tflops"] / mm["fp32"],
+                               "peak_source": "FP32 matmul (TF32 off) measured in this run"}
     return out
 
 
@@ -703,6 +736,55 @@ def fmm_matvec(m2l, device, precision, reps=5):
             "note": "P2M, M2M, M2L (levels 2-5), L2L, L2P and near field, particles resident on the GPU"}
 
 
+def direct_sum_at(pts, q, samp, device, chunk=16):
+    """f_i = sum_{j != i} q_j / |x_i - x_j| at the sampled particles (Eq. (1)),
+    in FP64 with torch on the GPU: the exact reference of the error figure
+    below (measurement only, not the product path)."""
+    import torch
+    x = torch.from_numpy(pts).to(device, torch.float64)
+    qq = torch.from_numpy(q).to(device, torch.float64)
+    out = []
+    for a in range(0, len(samp), chunk):
+        idx = torch.as_tensor(samp[a:a + chunk], device=device)
+        r = torch.cdist(x[idx], x)
+        inv = torch.where(r > 0, 1.0 / r, torch.zeros_like(r))
+        out.append(inv @ qq)
+    return torch.cat(out).cpu().numpy()
+
+
+def fmm_equal_error(m2l, device, precisions, nsamp=1000):
+    """The equal-error criterion of the metric, per M2L precision: the whole
+    GPU FMM matvec of the workload's particles (m2l_fmm_evaluate; FP64
+    particles and passes with the FP64 M2L, FP32 ones with the others) against
+    the direct sum at 1000 sampled particles.  A precision is at equal error
+    when its relative L2 error is within 10 % of the FP64 run's."""
+    import numpy as np
+    import torch
+
+    from paper_1210_7292_gb300 import synth
+    pts, q = synth.uniform_cube(N_PARTICLES, seed=SEED)
+    samp = np.sort(np.random.default_rng(12).choice(N_PARTICLES, nsamp, replace=False))
+    exact = direct_sum_at(pts, q, samp, device)
+    ops = m2l.m2l_precompute(m2l.M2L_K_INV_R, ELL)
+    err = {}
+    for fp64 in (True, False):
+        dt = torch.float64 if fp64 else torch.float32
+        xyz = torch.from_numpy(pts).to(device, dt)
+        qq = torch.from_numpy(q).to(device, dt)
+        fmm = m2l.m2l_fmm_create(ops, xyz, max(LEVELS))
+        for prec in (["fp64"] if fp64 else [p for p in precisions if p != "fp64"]):
+            phi = torch.zeros(N_PARTICLES, dtype=dt, device=device)
+            m2l.m2l_fmm_evaluate(fmm, xyz, qq, phi, prec)
+            got = phi.double().cpu().numpy()[samp]
+            err[prec] = float(np.linalg.norm(got - exact) / np.linalg.norm(exact))
+        del fmm
+    out = {"criterion": "rel. L2 vs the direct sum at %d sampled particles within 10 %% of the FP64 run's" % nsamp,
+           "rel_l2_vs_direct_sum": err}
+    out["ratio_to_fp64"] = {p: e / err["fp64"] for p, e in err.items()}
+    out["at_equal_error"] = {p: bool(e <= 1.10 * err["fp64"]) for p, e in err.items()}
+    return out
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_setup(args)
@@ -736,6 +818,7 @@ def run_ours(args):
     k5 = statistics.mean(kt[5])
     ach = FLOPS_PER_INTERACTION * wl.nint[5] / k5 / 1e12
     peaks, src_kind = measured_peaks()
+    mm = matmul_peaks(device)
 
     # end-to-end leg through host buffers
     for _ in range(2):
@@ -776,8 +859,10 @@ def run_ours(args):
     fmm = fmm_matvec(m2l, device, prec) if (rank == 0 and not args.quick and prec != "fp64") else None
     pre = precompute_times(m2l, device) if (rank == 0 and not args.quick) else None
     variants = variants_compare(m2l, device, wl, flush) if (rank == 0 and not args.quick) else None
-    dfmm = dfmm_m2l(m2l, device) if (rank == 0 and not args.quick) else None
+    dfmm = dfmm_m2l(m2l, device, mm) if (rank == 0 and not args.quick) else None
     cfg3 = config3_levels(m2l, device) if (rank == 0 and not args.quick) else None
+    eqerr = (fmm_equal_error(m2l, device, ["fp64", "fp32", "tf32x3", "bf16x3", "tf32"])
+             if (rank == 0 and not args.quick) else None)
     cpu = None
     if rank == 0 and world == 1 and not args.quick:
         cpu, ref_loc = cpu_oracle_sample(with_locals=True)
@@ -799,12 +884,14 @@ def run_ours(args):
                                   "interactions_per_s": wl.nint[L] / statistics.mean(kt[L]),
                                   "gflops": FLOPS_PER_INTERACTION * wl.nint[L] / statistics.mean(kt[L]) / 1e9}
                               for L in LEVELS},
-                "roofline": roofline(prec, ach, peaks, src_kind),
+                "roofline": roofline(prec, ach, peaks, src_kind, mm),
+                "matmul_peaks_tflops": mm,
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": "interactions/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches,
                 "fmm_matvec": fmm,
+                "equal_error": eqerr,
                 "precompute": pre,
                 "variants": variants,
                 "dfmm_m2l": dfmm,

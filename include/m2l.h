@@ -29,6 +29,12 @@
  *  - The transfer vector of a pair is t = X - Y (target minus source) in
  *    integer cell coordinates (Sec. 3.1).  Every list entry must satisfy
  *    |t|_inf in {2, 3}.
+ *  - An m2l_ops object belongs to the device that was current when it was
+ *    built.  Every entry point that launches work with it (directly, or through
+ *    a plan, batch, FMM or SA object built from it) first checks that the
+ *    calling thread's current device is that device and returns M2L_EINVAL,
+ *    launching nothing, when it is not.  Vectors, lists and streams passed
+ *    with it must live on the same device.
  *  - No exception crosses the ABI: every entry point returns an m2l_status;
  *    m2l_last_error() gives a message for the calling thread.  Errors found
  *    by a kernel (a list entry that is not a far-field pair, an index out of

@@ -76,9 +76,21 @@ static bool is_homogeneous(int kind, int *degree)
     return false;
 }
 
+m2l_status check_device(const m2l_ops *ops)
+{
+    int dev = -1;
+    M2L_CUDA(cudaGetDevice(&dev));
+    if (dev != ops->device) {
+        set_error("the current device is %d, but the operators live on device %d", dev, ops->device);
+        return M2L_EINVAL;
+    }
+    return M2L_OK;
+}
+
 static m2l_status check_level(const m2l_ops *ops, const m2l_level *lv, double *scale)
 {
     if (!ops || !lv) { set_error("null ops or level"); return M2L_EINVAL; }
+    if (m2l_status st = check_device(ops)) return st;
     if (!(lv->width > 0.0) || !isfinite(lv->width)) { set_error("level width must be positive"); return M2L_EINVAL; }
     if (lv->ncells_tgt < 0 || lv->ncells_src < 0 || lv->nnz < 0) { set_error("negative size"); return M2L_EINVAL; }
     if (lv->ncells_tgt >= (1 << kTgtBits) || lv->ncells_src >= (1 << kTgtBits)) {
@@ -106,6 +118,7 @@ static m2l_status dispatch(const m2l_ops *ops, const Buckets &b, const void *in,
                            int out_fp64, double scale, cudaStream_t s)
 {
     if (b.nnz > 0 && (!in || !out)) { set_error("null vector pointer"); return M2L_EINVAL; }
+    if (m2l_status st = check_device(ops)) return st;
     switch (precision) {
     case M2L_FP64:
     case M2L_FP32:

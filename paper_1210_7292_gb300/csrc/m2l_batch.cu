@@ -81,6 +81,7 @@ extern "C" m2l_status m2l_batch_create(const m2l_plan *const *plans, int nbatch,
         const m2l_plan *pl = plans[i];
         if (!pl || !in[i] || !out[i]) { set_error("null plan or vector in batch entry %d", i); return M2L_EINVAL; }
         const m2l_ops *ops = pl->ops;
+        if (m2l_status st = check_device(ops)) return st;
         if (ops->eps > 0) { set_error("the persistent batch takes full-rank operators"); return M2L_EUNSUPPORTED; }
         m2l_status st = prepare_simt_layout(ops, fp64, s);
         if (st != M2L_OK) return st;

@@ -604,6 +604,7 @@ m2l_status m2l_fmm_create(const m2l_ops *const *ops, int n_particles, const void
     for (int L = 2; L <= leaf_level; ++L) {
         const m2l_ops *o = ops[L - 2];
         if (!o) { set_error("null operators for level %d", L); return M2L_EINVAL; }
+        if (m2l_status st = check_device(o)) return st;
         if (o->ell != leaf_ops->ell || o->kind != leaf_ops->kind || o->c != leaf_ops->c) {
             set_error("the operators of all levels must share kernel and order");
             return M2L_EINVAL;

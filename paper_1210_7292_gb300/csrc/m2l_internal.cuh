@@ -10,6 +10,8 @@
 
 #include "../../include/m2l.h"
 
+struct m2l_ops;
+
 namespace m2l {
 
 // Device status word bits, set by kernels with atomicOr.
@@ -41,6 +43,8 @@ __host__ __device__ __forceinline__ int rec_g(int y)
 }
 
 void set_error(const char *fmt, ...);
+// M2L_EINVAL unless the calling thread's current device is the one that built ops
+m2l_status check_device(const m2l_ops *ops);
 m2l_status cuda_fail(cudaError_t e, const char *what);
 void count_launch(int n = 1);
 

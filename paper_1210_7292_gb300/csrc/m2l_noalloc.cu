@@ -70,6 +70,9 @@ extern "C" m2l_status m2l_apply_level_noalloc(const m2l_ops *ops, const m2l_leve
                                               float *locals, void *stream)
 {
     if (!ops || !lv) { set_error("null ops or level"); return M2L_EINVAL; }
+    // the scratch array is looked up on the current device, and the kernels read
+    // the operators and tables of the device that built ops: the two must agree
+    if (m2l_status st = check_device(ops)) return st;
     if (ops->ell > kNoallocMaxEll) {
         set_error("m2l_apply_level_noalloc supports ell <= %d, got %d", kNoallocMaxEll, ops->ell);
         return M2L_EUNSUPPORTED;

@@ -704,6 +704,7 @@ m2l_status m2l_sa_apply_level(const m2l_sa *sa_c, const m2l_level *level, const 
     m2l_sa *sa = const_cast<m2l_sa *>(sa_c);
     if (!sa || !level) { set_error("null SA or level"); return M2L_EINVAL; }
     const m2l_ops *ops = sa->ops;
+    if (m2l_status st = check_device(ops)) return st;
     if (level->ncells_tgt < 0 || level->ncells_src < 0 || level->nnz < 0 ||
         (level->nnz > 0 && (!level->il_sources || !level->il_offsets || !level->tgt_ijk || !level->src_ijk ||
                             !multipoles || !locals))) {

@@ -128,11 +128,24 @@ def _check(fn, status):
         raise M2LError(fn, status, lib().m2l_last_error().decode(errors="replace"))
 
 
-def _stream_ptr(stream):
+def _stream_ptr(stream, device_index=None):
     import torch
     if stream is None:
-        stream = torch.cuda.current_stream()
+        stream = torch.cuda.current_stream() if device_index is None else torch.cuda.current_stream(device_index)
+    elif device_index is not None:
+        _check_device(device_index, ("stream", stream))
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check_device(device_index, *named):
+    """Raises ValueError unless every (name, tensor or stream) lives on CUDA
+    device `device_index`, the device that owns the operators."""
+    for what, t in named:
+        if t is None:
+            continue
+        idx = t.device.index if hasattr(t, "device") else None
+        if idx is None or int(idx) != int(device_index):
+            raise ValueError("%s is on device %s, the operators on cuda:%d" % (what, idx, int(device_index)))
 
 
 def _dev_ptr(t, dtype=None, what="tensor"):
@@ -149,12 +162,18 @@ def _dev_ptr(t, dtype=None, what="tensor"):
 
 
 class Ops:
-    """Owner of an m2l_ops handle (freed with the object)."""
+    """Owner of an m2l_ops handle (freed with the object).  `device` is the CUDA
+    device that was current when the operators were built; the library refuses
+    to use them from another one."""
 
-    def __init__(self, handle, ell):
+    def __init__(self, handle, ell, device=None):
         self.handle = handle
         self.ell = ell
         self.n3 = ell ** 3
+        if device is None:
+            import torch
+            device = torch.cuda.current_device()
+        self.device = int(device)
 
     def __del__(self):
         h, self.handle = getattr(self, "handle", None), None
@@ -206,7 +225,7 @@ def m2l_ops_aca_info(ops: Ops):
 
 
 def m2l_ops_rebuild(ops: Ops, stream=None):
-    _check("m2l_ops_rebuild", lib().m2l_ops_rebuild(ops.handle, _stream_ptr(stream)))
+    _check("m2l_ops_rebuild", lib().m2l_ops_rebuild(ops.handle, _stream_ptr(stream, ops.device)))
 
 
 def m2l_ops_query(ops: Ops):
@@ -253,14 +272,16 @@ def _vec_dtypes(precision, out_fp64):
 def m2l_apply_level(ops: Ops, level: Level, multipoles, locals_, precision="fp32", locals_fp64=False, stream=None):
     p, tin, tout = _vec_dtypes(precision, locals_fp64)
     _check_shapes(ops, multipoles, locals_, level.struct.ncells_src, level.struct.ncells_tgt)
+    _check_level_device(ops, level, multipoles, locals_)
     _check("m2l_apply_level", lib().m2l_apply_level(
         ops.handle, ctypes.byref(level.struct), _dev_ptr(multipoles, tin, "multipoles"),
-        _dev_ptr(locals_, tout, "locals"), p, int(bool(locals_fp64)), _stream_ptr(stream)))
+        _dev_ptr(locals_, tout, "locals"), p, int(bool(locals_fp64)), _stream_ptr(stream, ops.device)))
 
 
 def m2l_classify_level(ops: Ops, level: Level, stream=None):
+    _check_level_device(ops, level)
     _check("m2l_classify_level", lib().m2l_classify_level(ops.handle, ctypes.byref(level.struct),
-                                                          _stream_ptr(stream)))
+                                                          _stream_ptr(stream, ops.device)))
     ops._classified = (level.struct.ncells_src, level.struct.ncells_tgt)
 
 
@@ -268,18 +289,26 @@ def m2l_apply_classified(ops: Ops, multipoles, locals_, precision="fp32", locals
     p, tin, tout = _vec_dtypes(precision, locals_fp64)
     nin, nout = getattr(ops, "_classified", (multipoles.shape[0], locals_.shape[0]))
     _check_shapes(ops, multipoles, locals_, nin, nout)
+    _check_device(ops.device, ("multipoles", multipoles), ("locals", locals_))
     _check("m2l_apply_classified", lib().m2l_apply_classified(
         ops.handle, _dev_ptr(multipoles, tin, "multipoles"), _dev_ptr(locals_, tout, "locals"), p,
-        int(bool(locals_fp64)), _stream_ptr(stream)))
+        int(bool(locals_fp64)), _stream_ptr(stream, ops.device)))
 
 
 def m2l_apply_level_adjoint(ops: Ops, level: Level, grad_locals, grad_multipoles, precision="fp32",
                             grad_fp64=False, stream=None):
     p, tin, tout = _vec_dtypes(precision, grad_fp64)
     _check_shapes(ops, grad_locals, grad_multipoles, level.struct.ncells_tgt, level.struct.ncells_src)
+    _check_level_device(ops, level, grad_locals, grad_multipoles)
     _check("m2l_apply_level_adjoint", lib().m2l_apply_level_adjoint(
         ops.handle, ctypes.byref(level.struct), _dev_ptr(grad_locals, tin, "grad_locals"),
-        _dev_ptr(grad_multipoles, tout, "grad_multipoles"), p, int(bool(grad_fp64)), _stream_ptr(stream)))
+        _dev_ptr(grad_multipoles, tout, "grad_multipoles"), p, int(bool(grad_fp64)), _stream_ptr(stream, ops.device)))
+
+
+def _check_level_device(ops, level, *vectors):
+    """The level's arrays and the vectors must be on the operators' device."""
+    _check_device(ops.device, *[(n, getattr(level, n)) for n in ("tgt_ijk", "src_ijk", "il_offsets", "il_sources")])
+    _check_device(ops.device, *[("vector %d" % i, v) for i, v in enumerate(vectors)])
 
 
 def _check_shapes(ops, vin, vout, nin, nout):
@@ -300,8 +329,9 @@ class Plan:
 
 def m2l_plan_create(ops: Ops, level: Level, adjoint=False, stream=None) -> Plan:
     h = ctypes.c_void_p()
+    _check_level_device(ops, level)
     _check("m2l_plan_create", lib().m2l_plan_create(ops.handle, ctypes.byref(level.struct), int(bool(adjoint)),
-                                                    _stream_ptr(stream), ctypes.byref(h)))
+                                                    _stream_ptr(stream, ops.device), ctypes.byref(h)))
     s = level.struct
     n_in, n_out = (s.ncells_tgt, s.ncells_src) if adjoint else (s.ncells_src, s.ncells_tgt)
     plan = Plan(h, ops, n_in, n_out)
@@ -312,15 +342,17 @@ def m2l_plan_create(ops: Ops, level: Level, adjoint=False, stream=None) -> Plan:
 def m2l_plan_apply(plan: Plan, vin, vout, precision="fp32", out_fp64=False, stream=None):
     p, tin, tout = _vec_dtypes(precision, out_fp64)
     _check_shapes(plan.ops, vin, vout, plan.n_in, plan.n_out)
+    _check_device(plan.ops.device, ("input vectors", vin), ("output vectors", vout))
     _check("m2l_plan_apply", lib().m2l_plan_apply(plan.handle, _dev_ptr(vin, tin, "input vectors"),
                                                   _dev_ptr(vout, tout, "output vectors"), p,
-                                                  int(bool(out_fp64)), _stream_ptr(stream)))
+                                                  int(bool(out_fp64)), _stream_ptr(stream, plan.ops.device)))
 
 
 def m2l_plan_classify(plan: Plan, level: Level, stream=None):
     """Re-classify `level` into `plan` on `stream` (no host synchronisation)."""
+    _check_level_device(plan.ops, level)
     _check("m2l_plan_classify", lib().m2l_plan_classify(plan.handle, ctypes.byref(level.struct),
-                                                        _stream_ptr(stream)))
+                                                        _stream_ptr(stream, plan.ops.device)))
     s = level.struct
     plan.n_in, plan.n_out = ((s.ncells_tgt, s.ncells_src) if getattr(plan, "adjoint", False)
                              else (s.ncells_src, s.ncells_tgt))
@@ -329,7 +361,7 @@ def m2l_plan_classify(plan: Plan, level: Level, stream=None):
 
 def m2l_ops_prepare(ops: Ops, precision="fp32", stream=None):
     """Build the operators' kernel layouts for `precision` on `stream`."""
-    _check("m2l_ops_prepare", lib().m2l_ops_prepare(ops.handle, PRECISIONS[precision], _stream_ptr(stream)))
+    _check("m2l_ops_prepare", lib().m2l_ops_prepare(ops.handle, PRECISIONS[precision], _stream_ptr(stream, ops.device)))
 
 
 def m2l_plan_query(plan: Plan):
@@ -413,13 +445,14 @@ def m2l_apply_level_noalloc(ops: Ops, level: Level, multipoles, locals_, stream=
     """FP32 level translation that allocates no device memory (see include/m2l.h)."""
     import torch
     _check_shapes(ops, multipoles, locals_, level.struct.ncells_src, level.struct.ncells_tgt)
+    _check_level_device(ops, level, multipoles, locals_)
     _check("m2l_apply_level_noalloc", lib().m2l_apply_level_noalloc(
         ops.handle, ctypes.byref(level.struct), _dev_ptr(multipoles, torch.float32, "multipoles"),
-        _dev_ptr(locals_, torch.float32, "locals"), _stream_ptr(stream)))
+        _dev_ptr(locals_, torch.float32, "locals"), _stream_ptr(stream, ops.device)))
 
 
 def m2l_sync_status(ops: Ops, stream=None):
-    _check("m2l_sync_status", lib().m2l_sync_status(ops.handle, _stream_ptr(stream)))
+    _check("m2l_sync_status", lib().m2l_sync_status(ops.handle, _stream_ptr(stream, ops.device)))
 
 
 M2L_DEBUG_STALL_PRODUCER = 1
@@ -553,9 +586,10 @@ def m2l_sa_apply_level(sa: SA, level: Level, multipoles, locals_, precision="fp3
                        stream=None):
     p, tin, tout = _vec_dtypes(precision, locals_fp64)
     _check_shapes(sa.ops, multipoles, locals_, level.struct.ncells_src, level.struct.ncells_tgt)
+    _check_level_device(sa.ops, level, multipoles, locals_)
     _check("m2l_sa_apply_level", lib().m2l_sa_apply_level(
         sa.handle, ctypes.byref(level.struct), _dev_ptr(multipoles, tin, "multipoles"),
-        _dev_ptr(locals_, tout, "locals"), p, int(bool(locals_fp64)), _stream_ptr(stream)))
+        _dev_ptr(locals_, tout, "locals"), p, int(bool(locals_fp64)), _stream_ptr(stream, sa.ops.device)))
 
 
 # ---------------------------------------------------------------- directional FMM (Helmholtz)

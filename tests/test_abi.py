@@ -98,3 +98,33 @@ def test_product_path_does_not_import_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "m2l_oracle" not in text, f
+
+
+def test_binding_rejects_vectors_on_another_device(monkeypatch):
+    """Operators built on one device are never used with tensors, lists or a
+    stream of another: the binding raises before it reaches the library (the
+    library refuses the same call itself when the current device differs)."""
+    from types import SimpleNamespace as NS
+
+    from paper_1210_7292_gb300 import m2l
+
+    def no_library():
+        raise AssertionError("the library was called")
+    monkeypatch.setattr(m2l, "lib", no_library)
+
+    def tensor(dev, rows, cols=64):
+        return NS(device=NS(index=dev), shape=(rows, cols))
+    ops = NS(handle=None, ell=4, n3=64, device=0)
+
+    def level(dev):
+        return NS(struct=NS(ncells_src=8, ncells_tgt=8), tgt_ijk=tensor(dev, 8, 3), src_ijk=tensor(dev, 8, 3),
+                  il_offsets=tensor(dev, 9, 1), il_sources=tensor(dev, 0, 1))
+    for lv, mp, loc in ((level(1), tensor(0, 8), tensor(0, 8)), (level(0), tensor(1, 8), tensor(0, 8)),
+                        (level(0), tensor(0, 8), tensor(1, 8))):
+        for call in (lambda: m2l.m2l_apply_level(ops, lv, mp, loc, "fp32"),
+                     lambda: m2l.m2l_apply_level_adjoint(ops, lv, loc, mp, "fp32"),
+                     lambda: m2l.m2l_apply_level_noalloc(ops, lv, mp, loc)):
+            with pytest.raises(ValueError, match="device"):
+                call()
+    with pytest.raises(ValueError, match="stream"):
+        m2l._stream_ptr(NS(device=NS(index=1), cuda_stream=0), 0)
