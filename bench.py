@@ -746,8 +746,12 @@ def direct_sum_at(pts, q, samp, device, chunk=16):
     out = []
     for a in range(0, len(samp), chunk):
         idx = torch.as_tensor(samp[a:a + chunk], device=device)
-        r = torch.cdist(x[idx], x)
-        inv = torch.where(r > 0, 1.0 / r, torch.zeros_like(r))
+        # differences taken directly (no |x|^2 + |y|^2 - 2 x.y expansion, which
+        # cancels for near pairs); the particle itself is excluded by index
+        d = x[idx][:, None, :] - x[None, :, :]
+        r = torch.sqrt((d * d).sum(dim=2))
+        inv = 1.0 / r
+        inv[torch.arange(len(idx), device=device), idx] = 0.0
         out.append(inv @ qq)
     return torch.cat(out).cpu().numpy()
 

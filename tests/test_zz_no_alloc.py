@@ -110,7 +110,7 @@ def test_noalloc_leaves_free_device_memory_unchanged(m2l):
     further calls allocate nothing: cudaMemGetInfo reports the same free bytes
     before and after each of two calls."""
     from paper_1210_7292_gb300 import synth
-    ell, level = 5, 4
+    ell, level = 5, 3
     cells = synth.full_grid(level)
     ops = gpu_ops(m2l, ell, 0, level)
     lv = make_level(m2l, cells, level)
