@@ -220,6 +220,14 @@ m2l_status m2l_plan_apply(const m2l_plan *plan, const void *in_vectors, void *ou
  * ([nvalid][3]: source index, target index, g, in execution order). */
 m2l_status m2l_plan_query(const m2l_plan *plan, int64_t *counts16, int32_t *records, int64_t *nvalid);
 void m2l_plan_free(m2l_plan *plan);
+/* Which kernel the tensor-core applies of a plan take.  *dense = 1 when the
+ * level was also classified for the target-stationary kernel (ell <= 5,
+ * full-rank operators, at least 2048 target cells whose lists hold at least
+ * half of the 189 far-field entries per cell of a full level, Sec. 3.2): its
+ * targets are grouped by octant into at most *units units of *unit_width
+ * columns.  *dense = 0: the operator-bucketed kernel.  Host-side only (no
+ * synchronisation); any output pointer may be NULL. */
+m2l_status m2l_plan_kernel_info(const m2l_plan *plan, int *dense, int *units, int *unit_width);
 /* Re-classify a level into an existing plan (step a3 of Alg. 2, as in
  * m2l_plan_create), asynchronously on `stream`: no host synchronisation, and
  * no allocation once the plan's buffers have held a classification of at
@@ -482,6 +490,10 @@ m2l_status m2l_apply_level_noalloc(const m2l_ops *ops, const m2l_level *level, c
  * m2l_sync_status reports M2L_ETIMEOUT.  Used to test failure detection
  * without faulting the GPU; the results of such a call are incomplete. */
 #define M2L_DEBUG_STALL_PRODUCER 1
+/* M2L_DEBUG_NO_DENSE makes the tensor-core precisions apply full levels with
+ * the operator-bucketed kernel instead of the target-stationary one, so that
+ * the two can be compared on the same plan (results agree to rounding). */
+#define M2L_DEBUG_NO_DENSE 2
 m2l_status m2l_ops_set_debug(m2l_ops *ops, int flags);
 
 /* ---------------------------------------------------------------------

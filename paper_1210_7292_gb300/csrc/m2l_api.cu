@@ -236,6 +236,7 @@ m2l_status m2l_ops_rebuild(m2l_ops *ops, void *stream)
     // derived layouts are rebuilt from the new masters on their next use
     ops->simt64.ready = ops->simt32.ready = false;
     ops->tc_tf32.ready = ops->tc_bf16x3.ready = ops->tc_tf32x3.ready = false;
+    ops->tcd_tf32.ready = ops->tcd_bf16x3.ready = ops->tcd_tf32x3.ready = false;
     return st;
 }
 
@@ -293,11 +294,12 @@ void m2l_ops_free(m2l_ops *ops)
     cudaDeviceSynchronize();
     ops->K64.release(); ops->sigma.release(); ops->lut.release(); ops->tsym.release();
     ops->U64.release(); ops->V64.release();
-    Layout *ls[] = {&ops->simt64, &ops->simt32, &ops->lr64, &ops->lr32, &ops->tc_tf32, &ops->tc_bf16x3, &ops->tc_tf32x3};
+    Layout *ls[] = {&ops->simt64, &ops->simt32, &ops->lr64, &ops->lr32, &ops->tc_tf32, &ops->tc_bf16x3, &ops->tc_tf32x3,
+                    &ops->tcd_tf32, &ops->tcd_bf16x3, &ops->tcd_tf32x3};
     for (Layout *l : ls) { l->a.release(); l->b.release(); }
     Buckets &b = ops->ws;
     b.rec.release(); b.tgt_of.release(); b.code.release(); b.seg.release(); b.class_off.release();
-    b.t_off.release(); b.t_src.release(); b.t_cursor.release();
+    b.t_off.release(); b.t_src.release(); b.t_cursor.release(); b.dense.release();
     if (ops->d_status) cudaFree(ops->d_status);
     delete ops;
 }
@@ -398,9 +400,12 @@ m2l_status m2l_plan_classify(m2l_plan *plan, const m2l_level *level, void *strea
 m2l_status m2l_ops_prepare(const m2l_ops *ops, int precision, void *stream)
 {
     if (!ops) { set_error("null ops"); return M2L_EINVAL; }
-    // an apply over no interactions builds the layouts and launches nothing else
+    // an apply over no interactions builds the layouts and launches nothing else;
+    // the tensor-core precisions also get the per-slot images of the dense kernel
     Buckets empty;
-    return dispatch(ops, empty, nullptr, nullptr, precision, 0, 1.0, (cudaStream_t)stream);
+    m2l_status st = dispatch(ops, empty, nullptr, nullptr, precision, 0, 1.0, (cudaStream_t)stream);
+    if (st != M2L_OK) return st;
+    return dense_prepare(ops, precision, (cudaStream_t)stream);
 }
 
 m2l_status m2l_plan_query(const m2l_plan *plan, int64_t *counts16, int32_t *records, int64_t *nvalid)
@@ -428,13 +433,23 @@ m2l_status m2l_plan_query(const m2l_plan *plan, int64_t *counts16, int32_t *reco
     return M2L_OK;
 }
 
+m2l_status m2l_plan_kernel_info(const m2l_plan *plan, int *dense, int *units, int *unit_width)
+{
+    if (!plan) { set_error("null plan"); return M2L_EINVAL; }
+    const DenseBuckets &d = plan->b.dense;
+    if (dense) *dense = d.valid ? 1 : 0;
+    if (units) *units = d.valid ? d.umax : 0;
+    if (unit_width) *unit_width = d.valid ? d.nu : 0;
+    return M2L_OK;
+}
+
 void m2l_plan_free(m2l_plan *plan)
 {
     if (!plan) return;
     cudaDeviceSynchronize();
     Buckets &b = plan->b;
     b.rec.release(); b.tgt_of.release(); b.code.release(); b.seg.release(); b.class_off.release();
-    b.t_off.release(); b.t_src.release(); b.t_cursor.release();
+    b.t_off.release(); b.t_src.release(); b.t_cursor.release(); b.dense.release();
     delete plan;
 }
 

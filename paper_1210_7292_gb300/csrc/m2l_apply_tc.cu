@@ -941,6 +941,10 @@ m2l_status launch_kind(const m2l_ops *ops, const Buckets &b, Layout &L, const fl
         return M2L_EUNSUPPORTED;
     }
     if (n3 > 128) return launch_big_ell<KIND>(ops, b, L, in, out, out_fp64, scale, s);
+    if (b.nnz > 0 && b.dense.valid && !(ops->debug_flags & M2L_DEBUG_NO_DENSE)) {
+        constexpr int prec = KIND == TC_TF32 ? M2L_TF32 : KIND == TC_BF16X3 ? M2L_BF16X3 : M2L_TF32X3;
+        return launch_tc_dense(ops, b.dense, prec, in, out, out_fp64, scale, s);
+    }
     const int katoms = tc_katoms<KIND>(n3);
     const int cols_part = tc_a_cols_part<KIND>(katoms);
     const size_t a_bytes = (size_t)Tr::nparts * 128 * cols_part * sizeof(uint32_t);

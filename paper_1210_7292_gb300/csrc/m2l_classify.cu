@@ -304,6 +304,7 @@ static m2l_status bucket(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const 
                          cudaStream_t s)
 {
     m2l_status st;
+    b.dense.valid = false;
     const int nseg = (nnz + kSegEntries - 1) / kSegEntries;
     if ((st = b.rec.ensure((size_t)(nnz > 0 ? nnz : 1) * sizeof(int2))) != M2L_OK) return st;
     if ((st = b.tgt_of.ensure((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t))) != M2L_OK) return st;
@@ -337,6 +338,9 @@ static m2l_status bucket(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const 
     scatter_kernel<<<nseg, kSegWarps * 32, 0, s>>>(nnz, nseg, b.code.as<uint16_t>(), b.tgt_of.as<int32_t>(), sources,
                                                     pos, b.class_off.as<int32_t>(), b.rec.as<int2>());
     M2L_LAUNCH_CHECK("scatter_kernel");
+    // full levels are also classified for the target-stationary tensor-core kernel
+    if (dense_eligible(ops, ntgt, nnz))
+        return dense_classify(ops, ntgt, nsrc, nnz, tgt_ijk, src_ijk, offsets, sources, b.dense, s);
     return M2L_OK;
 }
 

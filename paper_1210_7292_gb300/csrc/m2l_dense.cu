@@ -1,0 +1,715 @@
+// The target-stationary tensor-core M2L for full levels (ell <= 5).
+//
+// Alg. 2 blocks the interactions of one unique operator K_p along many target
+// cells (Sec. 4.2.3) and pays for it with a permutation of every source
+// vector (Eq. (30)) and of every result (Eq. (32)).  On the tcgen05 tensor
+// cores that per-column permutation work, not the product, bounds the
+// bucketed kernel.  This file moves the permutation onto the operator once
+// per transfer vector instead: K_t = P_t K_p P_t^T is written out, from the
+// 16 FP64 masters and the 48 tables sigma_g (Eq. (25)), as one pre-swizzled
+// operand image per t (K_t[a][b] = K_p[sigma(a)][sigma(b)]).  Then, for a
+// unit of up to nu target cells (columns) of one octant, every transfer
+// vector of the unit is one product D += K_t W_t, where column j of W_t is
+// the unpermuted multipole of the source X_j - t (zero if there is none);
+// the sum over the interaction list of Eq. (7) accumulates in TMEM and each
+// local is written once per launch.
+//
+// Classification (step a3 for this kernel): targets are ranked by the octant
+// of their cell (stable), each octant's run is split into balanced units,
+// and every list entry (X, Y) writes Y into tab[unit(X)][slot(t)][column(X)]
+// (slot(t) = (t1+3) + 7 (t2+3) + 49 (t3+3)).  Per unit the slots holding an
+// entry are listed in ascending order.
+//
+// Apply: the multipoles are first split once per call (hi/lo parts of
+// BF16x3 / TF32x3, the TF32 rounding of TF32) into rows of [parts][kpad]
+// plus one zero row.  One persistent CTA per SM walks its units; per unit
+// and active slot, a producer warp brings each 128-byte K column of the
+// slot's operator image into shared memory with one bulk copy and gathers
+// the nu source rows of the same K column with TMA tile::gather4 loads (4
+// rows per load, 128-byte swizzle, straight into the UMMA operand layout);
+// one thread of the MMA warp issues tcgen05.mma (M = 128, N = nu) into one
+// of two TMEM accumulators; four epilogue warps read a finished unit with
+// tcgen05.ld and add it, times w^degree, to the locals: one atomic add per
+// (target, node) and launch.  Every wait is bounded (about two seconds); on
+// expiry the CTA records M2L_ETIMEOUT, drains its own copies and MMAs,
+// frees TMEM and returns.
+#include <cuda.h>
+
+#include <mutex>
+
+#include "m2l_tcgen05.cuh"
+
+namespace m2l {
+namespace {
+
+constexpr int kSlots = 343;           // transfer-vector slots, |t_i| <= 3
+constexpr int kSlotRow = 344;         // per unit: count, then up to 343 slots
+constexpr int kDenseMinTargets = 2048;
+constexpr int kRankBlock = 256;       // targets per block of the octant ranking
+
+// ---------------------------------------------------------------- classification
+// Octant of every target cell and its stable rank among the targets of the
+// same octant within its block of kRankBlock targets; per-block octant counts.
+__global__ void __launch_bounds__(kRankBlock)
+dense_rank_kernel(int ntgt, int nblk, const int32_t *__restrict__ tgt_ijk, int32_t *__restrict__ rank,
+                  int32_t *__restrict__ bcnt)
+{
+    __shared__ int wcnt[kRankBlock / 32][8];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x = blockIdx.x * kRankBlock + threadIdx.x;
+    int o = 8;
+    if (x < ntgt)
+        o = (tgt_ijk[3 * x] & 1) | ((tgt_ijk[3 * x + 1] & 1) << 1) | ((tgt_ijk[3 * x + 2] & 1) << 2);
+    if (lane < 8) wcnt[w][lane] = 0;
+    __syncwarp();
+    const unsigned peers = __match_any_sync(0xffffffffu, o);
+    const int rw = __popc(peers & ((1u << lane) - 1u));
+    if (o < 8 && lane == __ffs(peers) - 1) wcnt[w][o] = __popc(peers);
+    __syncthreads();
+    if (o < 8) {
+        int r = rw;
+        for (int k = 0; k < w; ++k) r += wcnt[k][o];
+        rank[x] = r | (o << 16);
+    }
+    if (threadIdx.x < 8) {
+        int sum = 0;
+        for (int k = 0; k < kRankBlock / 32; ++k) sum += wcnt[k][threadIdx.x];
+        bcnt[(size_t)threadIdx.x * nblk + blockIdx.x] = sum;
+    }
+}
+
+// Units per octant from the scanned block counts (one thread).
+// meta: [0] units U, [1 + o] octant size n_o, [9 + o] octant start, [17 + o]
+// first unit of octant o, [25 + o] units m_o of octant o.
+__global__ void dense_meta_kernel(int nblk, int nu, const int32_t *__restrict__ bbase, int32_t *__restrict__ meta)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int u = 0;
+    const int total = bbase[8 * nblk];
+    for (int o = 0; o < 8; ++o) {
+        const int start = bbase[o * nblk];
+        const int end = (o < 7) ? bbase[(o + 1) * nblk] : total;
+        const int n = end - start;
+        const int m = (n + nu - 1) / nu;
+        meta[1 + o] = n;
+        meta[9 + o] = start;
+        meta[17 + o] = u;
+        meta[25 + o] = m;
+        u += m;
+    }
+    meta[0] = u;
+}
+
+// Unit and column of every target: octant o's run of n targets is split into m
+// units, unit k holding positions [floor(k n / m), floor((k + 1) n / m)).
+__global__ void dense_place_kernel(int ntgt, int nblk, int nu, const int32_t *__restrict__ rank,
+                                   const int32_t *__restrict__ bbase, const int32_t *__restrict__ meta,
+                                   int32_t *__restrict__ unit_col, int32_t *__restrict__ unit_tgt)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= ntgt) return;
+    const int rk = rank[x] & 0xFFFF, o = rank[x] >> 16;
+    const int blk = x / kRankBlock;
+    const long long n = meta[1 + o], m = meta[25 + o];
+    const long long pos = (long long)bbase[o * nblk + blk] + rk - meta[9 + o];
+    long long k = pos * m / n;
+    while (k + 1 < m && (k + 1) * n / m <= pos) ++k;
+    const int u = meta[17 + o] + (int)k;
+    const int j = (int)(pos - k * n / m);
+    unit_col[x] = (u << 9) | j;
+    unit_tgt[(size_t)u * nu + j] = x;
+}
+
+// One warp per target row of the CSR list: each entry (X, Y) writes Y + 1 into
+// tab[unit(X)][slot(t)][column(X)] and flags the slot of the unit.  Entries
+// that are not far-field pairs, indices out of range and repeated (X, t) pairs
+// set the status word and are skipped.
+__global__ void dense_fill_kernel(int ntgt, int nsrc, int nnz, int nu, const int32_t *__restrict__ offsets,
+                                  const int32_t *__restrict__ sources, const int32_t *__restrict__ tgt_ijk,
+                                  const int32_t *__restrict__ src_ijk, const uint16_t *__restrict__ lut,
+                                  const int32_t *__restrict__ unit_col, int32_t *__restrict__ tab,
+                                  int32_t *__restrict__ flags, int *__restrict__ status)
+{
+    const int x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (x >= ntgt) return;
+    const int o0 = offsets[x], o1 = offsets[x + 1];
+    if (o0 < 0 || o1 < o0 || o1 > nnz || (x == 0 && o0 != 0)) {
+        if (lane == 0) atomicOr(status, ST_BAD_INDEX);
+        return;
+    }
+    const int uc = unit_col[x];
+    const int u = uc >> 9, j = uc & 511;
+    const int xi = tgt_ijk[3 * x], xj = tgt_ijk[3 * x + 1], xk = tgt_ijk[3 * x + 2];
+    for (int e = o0 + lane; e < o1; e += 32) {
+        const int y = sources[e];
+        if (y < 0 || y >= nsrc) {
+            atomicOr(status, ST_BAD_INDEX);
+            continue;
+        }
+        const int t0 = xi - src_ijk[3 * y], t1 = xj - src_ijk[3 * y + 1], t2 = xk - src_ijk[3 * y + 2];
+        if (abs(t0) > 3 || abs(t1) > 3 || abs(t2) > 3) {
+            atomicOr(status, ST_BAD_PAIR);
+            continue;
+        }
+        const int slot = (t0 + 3) + 7 * (t1 + 3) + 49 * (t2 + 3);
+        if (lut[slot] == 0xFFFF) {
+            atomicOr(status, ST_BAD_PAIR);
+            continue;
+        }
+        const int prev = atomicExch(tab + ((size_t)u * kSlots + slot) * nu + j, y + 1);
+        if (prev != 0) atomicOr(status, ST_BAD_PAIR);   // the same (X, t) twice
+        flags[(size_t)u * kSlots + slot] = 1;
+    }
+}
+
+// One warp per unit: the flagged slots in ascending order, count first.
+__global__ void dense_slots_kernel(int umax, const int32_t *__restrict__ meta, const int32_t *__restrict__ flags,
+                                   uint16_t *__restrict__ slots)
+{
+    const int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (u >= umax) return;
+    uint16_t *row = slots + (size_t)u * kSlotRow;
+    if (u >= meta[0]) {
+        if (lane == 0) row[0] = 0;
+        return;
+    }
+    int n = 0;
+    for (int c = 0; c < kSlots; c += 32) {
+        const int slot = c + lane;
+        const bool f = slot < kSlots && flags[(size_t)u * kSlots + slot] != 0;
+        const unsigned m = __ballot_sync(0xffffffffu, f);
+        if (f) row[1 + n + __popc(m & ((1u << lane) - 1u))] = (uint16_t)slot;
+        n += __popc(m);
+    }
+    if (lane == 0) row[0] = (uint16_t)n;
+}
+
+}  // namespace
+
+bool dense_eligible(const m2l_ops *ops, int ntgt, int nnz)
+{
+    // 189 far-field transfer vectors per target cell in a full level (Sec. 3.2):
+    // the kernel pays for every (target, active t) column, so it takes levels
+    // whose lists are at least half full and large enough to fill the GPU
+    return ops->eps <= 0.0 && ops->n3 <= 128 && ntgt >= kDenseMinTargets && (double)nnz >= 0.5 * 189.0 * ntgt;
+}
+
+// Columns per unit: balance ~ntgt/8 targets per octant over the SMs, counting
+// a unit's operator traffic as 64 columns of its own.
+static int choose_nu(int ntgt)
+{
+    const int nsm = num_sms();
+    const long per_oct = (ntgt + 7) / 8;
+    int best = 256;
+    long best_cost = -1;
+    for (int nu = 256; nu >= 32; nu -= 16) {
+        const long units = 8 * ((per_oct + nu - 1) / nu);
+        const long rounds = (units + nsm - 1) / nsm;
+        const long cost = rounds * (nu + 64);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = nu;
+        }
+    }
+    return best;
+}
+
+m2l_status dense_classify(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const int32_t *tgt_ijk,
+                          const int32_t *src_ijk, const int32_t *offsets, const int32_t *sources, DenseBuckets &d,
+                          cudaStream_t s)
+{
+    m2l_status st;
+    const int nu = choose_nu(ntgt);
+    const int umax = (ntgt + nu - 1) / nu + 8;
+    const int nblk = (ntgt + kRankBlock - 1) / kRankBlock;
+    if (umax >= (1 << 22)) {
+        set_error("too many target units for the dense classification");
+        return M2L_EUNSUPPORTED;
+    }
+    // work: rank [ntgt], unit_col [ntgt], bcnt [8 nblk + 1], bbase [8 nblk + 1], flags [umax][343]
+    const size_t n_work = 2 * (size_t)ntgt + 2 * (8 * (size_t)nblk + 1) + (size_t)umax * kSlots;
+    if ((st = d.work.ensure(n_work * sizeof(int32_t))) != M2L_OK) return st;
+    if ((st = d.unit_tgt.ensure((size_t)umax * nu * sizeof(int32_t))) != M2L_OK) return st;
+    if ((st = d.tab.ensure((size_t)umax * kSlots * nu * sizeof(int32_t))) != M2L_OK) return st;
+    if ((st = d.slots.ensure((size_t)umax * kSlotRow * sizeof(uint16_t))) != M2L_OK) return st;
+    if ((st = d.meta.ensure(64 * sizeof(int32_t))) != M2L_OK) return st;
+    // split multipoles of any precision: up to two parts of 128 four-byte values per row
+    if ((st = d.bsplit.ensure(((size_t)nsrc + 1) * 1024)) != M2L_OK) return st;
+    d.umax = umax;
+    d.nu = nu;
+    d.ntgt = ntgt;
+    d.nsrc = nsrc;
+    d.nnz = nnz;
+    d.valid = true;
+    int32_t *rank = d.work.as<int32_t>();
+    int32_t *unit_col = rank + ntgt;
+    int32_t *bcnt = unit_col + ntgt;
+    int32_t *bbase = bcnt + 8 * (size_t)nblk + 1;
+    int32_t *flags = bbase + 8 * (size_t)nblk + 1;
+    M2L_CUDA(cudaMemsetAsync(d.tab.p, 0, (size_t)umax * kSlots * nu * sizeof(int32_t), s));
+    M2L_CUDA(cudaMemsetAsync(flags, 0, (size_t)umax * kSlots * sizeof(int32_t), s));
+    M2L_CUDA(cudaMemsetAsync(d.unit_tgt.p, 0xFF, (size_t)umax * nu * sizeof(int32_t), s));
+    dense_rank_kernel<<<nblk, kRankBlock, 0, s>>>(ntgt, nblk, tgt_ijk, rank, bcnt);
+    M2L_LAUNCH_CHECK("dense_rank_kernel");
+    if ((st = launch_exclusive_scan(bcnt, bbase, 8 * nblk, s)) != M2L_OK) return st;
+    dense_meta_kernel<<<1, 32, 0, s>>>(nblk, nu, bbase, d.meta.as<int32_t>());
+    M2L_LAUNCH_CHECK("dense_meta_kernel");
+    dense_place_kernel<<<(ntgt + 255) / 256, 256, 0, s>>>(ntgt, nblk, nu, rank, bbase, d.meta.as<int32_t>(),
+                                                           unit_col, d.unit_tgt.as<int32_t>());
+    M2L_LAUNCH_CHECK("dense_place_kernel");
+    if (nnz > 0) {
+        const int blocks = (int)(((long)ntgt * 32 + 255) / 256);
+        dense_fill_kernel<<<blocks, 256, 0, s>>>(ntgt, nsrc, nnz, nu, offsets, sources, tgt_ijk, src_ijk,
+                                                 ops->lut.as<uint16_t>(), unit_col, d.tab.as<int32_t>(), flags,
+                                                 ops->d_status);
+        M2L_LAUNCH_CHECK("dense_fill_kernel");
+    }
+    dense_slots_kernel<<<(umax * 32 + 255) / 256, 256, 0, s>>>(umax, d.meta.as<int32_t>(), flags,
+                                                                d.slots.as<uint16_t>());
+    M2L_LAUNCH_CHECK("dense_slots_kernel");
+    return M2L_OK;
+}
+
+namespace {
+
+// K columns (swizzle columns of 128 bytes) per operator row: kpad = katoms * (128 / esz).
+template <int KIND>
+__host__ __device__ constexpr int dense_katoms(int n3)
+{
+    return (n3 * TcTraits<KIND>::esz + 127) / 128;
+}
+
+// Operator image of every transfer-vector slot: K_t[a][b] = K_p[sigma_g(a)][sigma_g(b)]
+// for (p, g) = lut[slot] (Eq. (25) with the orientation of the permutation
+// tables), rows a < 128 (zero beyond ell^3), K padded with zeros to katoms
+// swizzle columns.  Layout per slot: [katom][part][128 rows x 128 bytes],
+// each block 128-byte swizzled (K-major UMMA operand), so that one K column
+// of both parts is one contiguous bulk copy.  Slots without an operator (the
+// near field) are left untouched and never read.
+template <int KIND>
+__global__ void dense_image_kernel(int n3, int katoms, const double *__restrict__ K, const int16_t *__restrict__ sigma,
+                                   const uint16_t *__restrict__ lut, uint8_t *__restrict__ img)
+{
+    using Tr = TcTraits<KIND>;
+    constexpr int E = 128 / Tr::esz;
+    const int slot = blockIdx.y;
+    const uint16_t c = lut[slot];
+    if (c == 0xFFFF) return;
+    const int p = c & 0xFF, g = c >> 8;
+    const int kpad = katoms * E;
+    const int16_t *sg = sigma + (size_t)g * n3;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 128 * kpad; idx += gridDim.x * blockDim.x) {
+        const int row = idx / kpad, kk = idx % kpad;
+        const double x = (row < n3 && kk < n3) ? K[((size_t)p * n3 + sg[row]) * n3 + sg[kk]] : 0.0;
+        const int ka = kk / E, e = kk % E;
+        const int chunk = e / (16 / Tr::esz), within = e % (16 / Tr::esz);
+        uint8_t *blk = img + ((size_t)slot * katoms + ka) * (Tr::nparts * 16384);
+        const uint32_t off = swz_off(row, chunk) + (uint32_t)(within * Tr::esz);
+        if constexpr (KIND == TC_BF16X3) {
+            const __nv_bfloat16 h = __double2bfloat16(x);
+            const __nv_bfloat16 l = __double2bfloat16(x - (double)__bfloat162float(h));
+            *reinterpret_cast<__nv_bfloat16 *>(blk + off) = h;
+            *reinterpret_cast<__nv_bfloat16 *>(blk + 16384 + off) = l;
+        } else if constexpr (KIND == TC_TF32) {
+            *reinterpret_cast<float *>(blk + off) = tf32_rna((float)x);
+        } else {
+            const float h = tf32_rna((float)x);
+            const float l = tf32_rna((float)(x - (double)h));
+            *reinterpret_cast<float *>(blk + off) = h;
+            *reinterpret_cast<float *>(blk + 16384 + off) = l;
+        }
+    }
+}
+
+// The multipoles as TMA-gatherable rows: row y = [part][kpad] of the split
+// values of multipole y (hi = round(x), lo = round(x - hi) for the split
+// precisions, the TF32 rounding for TF32), zero-padded; row nsrc is zero.
+template <int KIND>
+__global__ void dense_split_kernel(int nsrc, int n3, int kpad, const float *__restrict__ in, uint8_t *__restrict__ out)
+{
+    using Tr = TcTraits<KIND>;
+    const size_t row_bytes = (size_t)Tr::nparts * kpad * Tr::esz;
+    const long total = (long)(nsrc + 1) * kpad;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int y = (int)(idx / kpad), k = (int)(idx % kpad);
+        const float x = (y < nsrc && k < n3) ? in[(size_t)y * n3 + k] : 0.0f;
+        uint8_t *r = out + (size_t)y * row_bytes + (size_t)k * Tr::esz;
+        if constexpr (KIND == TC_BF16X3) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+            *reinterpret_cast<__nv_bfloat16 *>(r) = h;
+            *reinterpret_cast<__nv_bfloat16 *>(r + (size_t)kpad * 2) = l;
+        } else if constexpr (KIND == TC_TF32) {
+            *reinterpret_cast<float *>(r) = tf32_rna(x);
+        } else {
+            const float h = tf32_rna(x);
+            *reinterpret_cast<float *>(r) = h;
+            *reinterpret_cast<float *>(r + (size_t)kpad * 4) = tf32_rna(x - h);
+        }
+    }
+}
+
+// tile::gather4: four rows (y0..y3) of the box [x, x + 128 bytes) of a 2-D
+// tensor into four consecutive 128-byte rows of shared memory at dst, with
+// the tensor map's 128-byte swizzle; completion counted on bar.
+__device__ __forceinline__ void tma_gather4(void *dst, const CUtensorMap *map, int x, int y0, int y1, int y2, int y3,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y0), "r"(y1), "r"(y2), "r"(y3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+constexpr int kDenseThreads = 192;    // warp 0 TMA producer, warp 1 MMA, warps 2-5 epilogue
+constexpr int kDenseEpiWarp0 = 2;
+constexpr int kDenseMaxStages = 4;
+constexpr int kDenseDStride = 256;    // TMEM columns between the two accumulators
+
+template <int KIND>
+__host__ __device__ constexpr int dense_stage_bytes(int nu)
+{
+    // one K column (128 bytes) of the operator (128 rows) and of nu gathered columns, all parts
+    return TcTraits<KIND>::nparts * 128 * (128 + nu);
+}
+
+// One persistent CTA per SM over units blockIdx.x, blockIdx.x + gridDim.x, ...
+// Shared memory: nstages stages of [operator K column: parts x 128 rows x 128 B]
+// [gathered K column: parts x nu rows x 128 B], then the mbarriers.  TMEM: two
+// accumulators of nu columns, 256 apart.
+template <int KIND>
+__global__ void __launch_bounds__(kDenseThreads, 1)
+tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restrict__ a_img,
+                const int32_t *__restrict__ meta, const uint16_t *__restrict__ slots, const int32_t *__restrict__ tab,
+                const int32_t *__restrict__ unit_tgt, int nu, int katoms, int nstages, int nsrc, int n3,
+                float *__restrict__ out_f32, double *__restrict__ out_f64, float scale, int *status,
+                int stall_first_stage)
+{
+    using Tr = TcTraits<KIND>;
+    constexpr int E = 128 / Tr::esz;               // K elements per swizzle column
+    constexpr int A_PART = 128 * 128;              // one part of an operator K column
+    constexpr int A_BYTES = Tr::nparts * A_PART;
+    constexpr int K_STEPS = 128 / 32;              // MMAs (32 bytes of K each) per swizzle column
+    const int b_part = nu * 128;                   // one part of a gathered K column
+    const int stage_bytes = A_BYTES + Tr::nparts * b_part;
+    const int kpad = katoms * E;
+    const int ngrp = nu / 4;                       // gather4 loads per part
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)nstages * stage_bytes);
+    uint64_t *full = bars, *empty = bars + kDenseMaxStages, *dfull = bars + 2 * kDenseMaxStages;
+    uint64_t *dempty = dfull + 2, *drain = dempty + 2;
+    __shared__ uint32_t s_tmem_base;
+    __shared__ int s_abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nunits = meta[0];
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int i = 0; i < nstages; ++i) {
+            mbar_init(full + i, 1);
+            mbar_init(empty + i, 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(dfull + i, 1);
+            mbar_init(dempty + i, 4 * 32);
+        }
+        mbar_init(drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem_base)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = s_tmem_base;
+    volatile int *abort_flag = &s_abort;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- TMA producer
+        long it = 0;
+        unsigned issued = 0, parity = 0;   // per stage: a fill is outstanding or done; its phase parity
+        bool stop = false;
+        for (int u = blockIdx.x; u < nunits && !stop; u += gridDim.x) {
+            const uint16_t *row = slots + (size_t)u * kSlotRow;
+            const int ns = row[0];
+            for (int si = 0; si < ns && !stop; ++si) {
+                const int slot = row[1 + si];
+                const int4 *tab4 = reinterpret_cast<const int4 *>(tab + ((size_t)u * kSlots + slot) * nu);
+                for (int ka = 0; ka < katoms; ++ka, ++it) {
+                    const int s = (int)(it % nstages);
+                    const uint32_t ph = (uint32_t)((it / nstages) & 1);
+                    int ok = 1;
+                    if (lane == 0) ok = mbar_wait(empty + s, ph ^ 1, abort_flag, status) ? 1 : 0;
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    if (!ok) {
+                        stop = true;
+                        break;
+                    }
+                    // test switch: withholding the first stage makes the MMA warp's wait run out
+                    if (stall_first_stage && it == 0) continue;
+                    uint8_t *st = smem + (size_t)s * stage_bytes;
+                    if (lane == 0) {
+                        mbar_arrive_expect_tx(full + s, (uint32_t)stage_bytes);
+                        bulk_g2s(st, a_img + ((size_t)slot * katoms + ka) * A_BYTES, A_BYTES, full + s);
+                    }
+                    __syncwarp();
+                    for (int q = lane; q < ngrp * Tr::nparts; q += 32) {
+                        const int part = q / ngrp, grp = q - part * ngrp;
+                        const int4 v = __ldg(tab4 + grp);
+                        tma_gather4(st + A_BYTES + part * b_part + grp * 512, &bmap, part * kpad + ka * E,
+                                    v.x ? v.x - 1 : nsrc, v.y ? v.y - 1 : nsrc, v.z ? v.z - 1 : nsrc,
+                                    v.w ? v.w - 1 : nsrc, full + s);
+                    }
+                    issued |= 1u << s;
+                    parity = (parity & ~(1u << s)) | (ph << s);
+                }
+            }
+        }
+        // every copy this CTA issued lands before its shared memory is released
+        if (lane == 0)
+            for (int s = 0; s < nstages; ++s)
+                if (issued & (1u << s)) mbar_wait_drain(full + s, (parity >> s) & 1u, status);
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA issue
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc(Tr::fmt, nu);
+            long it = 0;
+            int uc = 0;
+            bool issued = false, stop = false;
+            for (int u = blockIdx.x; u < nunits && !stop; u += gridDim.x) {
+                const uint16_t *row = slots + (size_t)u * kSlotRow;
+                const int ns = row[0];
+                if (ns == 0) continue;
+                const int b = uc & 1;
+                if (!mbar_wait(dempty + b, ((uc >> 1) & 1) ^ 1, abort_flag, status)) break;
+                tc_fence_after();
+                const uint32_t d = tmem_base + (uint32_t)(b * kDenseDStride);
+                uint32_t accum = 0;
+                for (int si = 0; si < ns && !stop; ++si) {
+                    for (int ka = 0; ka < katoms; ++ka, ++it) {
+                        const int s = (int)(it % nstages);
+                        if (!mbar_wait(full + s, (uint32_t)((it / nstages) & 1), abort_flag, status)) {
+                            stop = true;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sa = smem_u32(smem + (size_t)s * stage_bytes);
+                        const uint32_t sb = sa + (uint32_t)A_BYTES;
+#pragma unroll
+                        for (int k = 0; k < K_STEPS; ++k) {
+                            const uint64_t a0 = smem_desc(sa + 32 * k), b0 = smem_desc(sb + 32 * k);
+                            umma<KIND>(d, a0, b0, idesc, accum);
+                            accum = 1;
+                            if constexpr (Tr::nprod == 3) {
+                                // hi * lo and lo * hi into the same accumulator
+                                umma<KIND>(d, a0, smem_desc(sb + (uint32_t)b_part + 32 * k), idesc, 1);
+                                umma<KIND>(d, smem_desc(sa + A_PART + 32 * k), b0, idesc, 1);
+                            }
+                        }
+                        umma_commit(empty + s);
+                        issued = true;
+                    }
+                }
+                if (stop) break;
+                umma_commit(dfull + b);
+                ++uc;
+            }
+            if (issued) {
+                // every MMA issued by this thread has completed before TMEM is freed
+                umma_commit(drain);
+                mbar_wait_drain(drain, 0, status);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const int q = warp & 3;                // TMEM lane quarter of this warp
+        const int node = 32 * q + lane;        // accumulator row = local node index
+        int uc = 0;
+        for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+            const int ns = slots[(size_t)u * kSlotRow];
+            if (ns == 0) continue;
+            const int b = uc & 1;
+            const bool ok = mbar_wait(dfull + b, (uint32_t)((uc >> 1) & 1), abort_flag, status);
+            if (!__all_sync(0xffffffffu, ok)) break;   // tcgen05.ld below is warp-collective
+            tc_fence_after();
+            const int32_t *tg = unit_tgt + (size_t)u * nu;
+            for (int c0 = 0; c0 < nu; c0 += 16) {
+                float v[16];
+                tmem_ld<16>(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kDenseDStride + c0), v);
+                const int tl = tg[c0 + (lane & 15)];
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) {
+                    const int t = __shfl_sync(0xffffffffu, tl, jj);
+                    if (t >= 0 && node < n3) {
+                        if (out_f64) atomicAdd(out_f64 + (size_t)t * n3 + node, (double)v[jj] * (double)scale);
+                        else atomicAdd(out_f32 + (size_t)t * n3 + node, v[jj] * scale);
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(dempty + b);
+            ++uc;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512) : "memory");
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the library
+// links only the CUDA runtime).
+m2l_status encode_fn(EncodeTiled *out)
+{
+    static std::once_flag once;
+    static EncodeTiled fn = nullptr;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        err = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        if (err == cudaSuccess && q != cudaDriverEntryPointSuccess) err = cudaErrorSymbolNotFound;
+        fn = reinterpret_cast<EncodeTiled>(p);
+    });
+    if (err != cudaSuccess || !fn) return cuda_fail(err != cudaSuccess ? err : cudaErrorSymbolNotFound,
+                                                    "cuTensorMapEncodeTiled entry point");
+    *out = fn;
+    return M2L_OK;
+}
+
+template <int KIND> struct DensePrec;
+template <> struct DensePrec<TC_TF32> { static constexpr int value = M2L_TF32; };
+template <> struct DensePrec<TC_BF16X3> { static constexpr int value = M2L_BF16X3; };
+template <> struct DensePrec<TC_TF32X3> { static constexpr int value = M2L_TF32X3; };
+
+Layout &dense_layout(const m2l_ops *ops, int kind)
+{
+    m2l_ops *o = const_cast<m2l_ops *>(ops);
+    return kind == TC_TF32 ? o->tcd_tf32 : kind == TC_BF16X3 ? o->tcd_bf16x3 : o->tcd_tf32x3;
+}
+
+template <int KIND>
+m2l_status dense_images(const m2l_ops *ops, cudaStream_t s)
+{
+    using Tr = TcTraits<KIND>;
+    Layout &L = dense_layout(ops, KIND);
+    if (L.ready) return M2L_OK;
+    const int katoms = dense_katoms<KIND>(ops->n3);
+    const size_t bytes = (size_t)kSlots * katoms * Tr::nparts * 16384;
+    m2l_status st;
+    if ((st = L.a.ensure(bytes)) != M2L_OK) return st;
+    const int kpad = katoms * (128 / Tr::esz);
+    dim3 grid((unsigned)((128 * kpad + 255) / 256), kSlots);
+    dense_image_kernel<KIND><<<grid, 256, 0, s>>>(ops->n3, katoms, ops->K64.as<double>(), ops->sigma.as<int16_t>(),
+                                                  ops->lut.as<uint16_t>(), L.a.as<uint8_t>());
+    M2L_LAUNCH_CHECK("dense_image_kernel");
+    L.ready = true;
+    return M2L_OK;
+}
+
+template <int KIND>
+m2l_status launch_dense_kind(const m2l_ops *ops, const DenseBuckets &d, const float *in, void *out, int out_fp64,
+                             double scale, cudaStream_t s)
+{
+    using Tr = TcTraits<KIND>;
+    m2l_status st = dense_images<KIND>(ops, s);
+    if (st != M2L_OK) return st;
+    const int n3 = ops->n3, katoms = dense_katoms<KIND>(n3), kpad = katoms * (128 / Tr::esz);
+    const int row_bytes = Tr::nparts * kpad * Tr::esz;
+    if (((size_t)d.nsrc + 1) * row_bytes > d.bsplit.bytes || d.nu % 16 != 0 || d.nu > kDenseDStride) {
+        set_error("dense classification does not fit this precision");
+        return M2L_EINVAL;
+    }
+    const long total = (long)(d.nsrc + 1) * kpad;
+    const int sblocks = (int)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
+    dense_split_kernel<KIND><<<sblocks, 256, 0, s>>>(d.nsrc, n3, kpad, in, d.bsplit.as<uint8_t>());
+    M2L_LAUNCH_CHECK("dense_split_kernel");
+
+    EncodeTiled encode = nullptr;
+    if ((st = encode_fn(&encode)) != M2L_OK) return st;
+    alignas(64) CUtensorMap map;
+    const cuuint64_t gdim[2] = {(cuuint64_t)Tr::nparts * kpad, (cuuint64_t)d.nsrc + 1};
+    const cuuint64_t gstride[1] = {(cuuint64_t)row_bytes};
+    const cuuint32_t box[2] = {(cuuint32_t)(128 / Tr::esz), 1};
+    const cuuint32_t estride[2] = {1, 1};
+    const CUresult r = encode(&map, Tr::esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                              d.bsplit.p, gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return M2L_ECUDA;
+    }
+    const int stage = dense_stage_bytes<KIND>(d.nu);
+    const int budget = max_smem_optin() - 1024 - 256;
+    int nst = budget / stage;
+    if (nst > kDenseMaxStages) nst = kDenseMaxStages;
+    if (nst < 2) {
+        set_error("dense tensor-core kernel: %d-byte stages do not fit shared memory twice", stage);
+        return M2L_EUNSUPPORTED;
+    }
+    // at least half the SM's shared memory, so that one CTA (and one TMEM allocation) runs per SM
+    int smem = 1024 + nst * stage + 256;
+    if (smem < 120 * 1024) smem = 120 * 1024;
+    auto kern = tc_dense_kernel<KIND>;
+    M2L_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int grid = num_sms();
+    if (grid > d.umax) grid = d.umax;
+    const Layout &L = dense_layout(ops, KIND);
+    kern<<<grid, kDenseThreads, smem, s>>>(map, L.a.as<uint8_t>(), d.meta.as<int32_t>(), d.slots.as<uint16_t>(),
+                                          d.tab.as<int32_t>(), d.unit_tgt.as<int32_t>(), d.nu, katoms, nst, d.nsrc,
+                                          n3, out_fp64 ? nullptr : (float *)out, out_fp64 ? (double *)out : nullptr,
+                                          (float)scale, ops->d_status,
+                                          (ops->debug_flags & M2L_DEBUG_STALL_PRODUCER) ? 1 : 0);
+    M2L_LAUNCH_CHECK("tc_dense_kernel");
+    return M2L_OK;
+}
+
+}  // namespace
+
+m2l_status dense_prepare(const m2l_ops *ops, int precision, cudaStream_t s)
+{
+    if (ops->eps > 0 || ops->n3 > 128) return M2L_OK;
+    switch (precision) {
+    case M2L_TF32: return dense_images<TC_TF32>(ops, s);
+    case M2L_BF16X3: return dense_images<TC_BF16X3>(ops, s);
+    case M2L_TF32X3: return dense_images<TC_TF32X3>(ops, s);
+    default: return M2L_OK;
+    }
+}
+
+m2l_status launch_tc_dense(const m2l_ops *ops, const DenseBuckets &d, int precision, const float *in, void *out,
+                           int out_fp64, double scale, cudaStream_t s)
+{
+    switch (precision) {
+    case M2L_TF32: return launch_dense_kind<TC_TF32>(ops, d, in, out, out_fp64, scale, s);
+    case M2L_BF16X3: return launch_dense_kind<TC_BF16X3>(ops, d, in, out, out_fp64, scale, s);
+    case M2L_TF32X3: return launch_dense_kind<TC_TF32X3>(ops, d, in, out, out_fp64, scale, s);
+    default:
+        set_error("not a tensor-core precision: %d", precision);
+        return M2L_EINVAL;
+    }
+}
+
+}  // namespace m2l

@@ -88,6 +88,26 @@ struct ScratchGuard {
     ScratchGuard &operator=(const ScratchGuard &) = delete;
 };
 
+// Output of the dense classification (step a3 for full levels, used by the
+// target-stationary tensor-core kernel): targets grouped by the octant of
+// their cell into units of at most nu columns; per unit and transfer-vector
+// slot (the 343-entry index of t), the source of every column.
+struct DenseBuckets {
+    DevBuf unit_tgt;   // int32 [umax][nu]: target index of each column, -1 for padding
+    DevBuf tab;        // int32 [umax][343][nu]: source index + 1 of each column and slot, 0 = none
+    DevBuf slots;      // uint16 [umax][344]: [0] number of active slots, then the slots ascending
+    DevBuf meta;       // int32 [64]: [0] = number of units; per octant counts, starts, unit offsets
+    DevBuf work;       // int32 scratch: per-target ranks and (unit, column), block counts, slot flags
+    DevBuf bsplit;     // split multipoles [nsrc + 1][parts][kpad] of the last apply (row nsrc = 0)
+    int umax = 0, nu = 0, ntgt = 0, nsrc = 0, nnz = 0;
+    bool valid = false;
+    void release()
+    {
+        unit_tgt.release(); tab.release(); slots.release(); meta.release(); work.release(); bsplit.release();
+        valid = false;
+    }
+};
+
 // Output of the classification and bucketing (step a3).
 struct Buckets {
     DevBuf rec;        // int2 [nnz]: .x = source index, .y = target | g << 26, bucketed
@@ -97,6 +117,7 @@ struct Buckets {
     DevBuf class_off;  // int32 [18]: start of bucket p at [p], [16] = valid total, [17] = nnz
     // adjoint: transposed list (scratch)
     DevBuf t_off, t_src, t_cursor;
+    DenseBuckets dense;   // also filled for full levels that the dense kernel serves
     int nnz = 0;
     int ntgt = 0;
     int nsrc = 0;
@@ -128,6 +149,7 @@ struct m2l_ops {
     m2l::DevBuf tsym;         // int32 [16][3]
     m2l::DevBuf U64, V64;     // double [16][n3][rmax] (low rank; zero-padded columns)
     m2l::Layout simt64, simt32, lr64, lr32, tc_tf32, tc_bf16x3, tc_tf32x3;
+    m2l::Layout tcd_tf32, tcd_bf16x3, tcd_tf32x3;   // per-slot operator images of the dense kernel
     mutable m2l::Buckets ws;  // workspace of m2l_apply_level
     mutable double ws_scale = 1.0;  // scale of the level last classified into ws
     int lowrank_method = 0;   // 0: truncated SVD, 1: ACA + truncated SVD
@@ -169,6 +191,15 @@ m2l_status launch_tc(const m2l_ops *ops, const Buckets &b, const void *in, void 
 
 int num_sms();
 int max_smem_optin();
+
+// Dense classification and the target-stationary tensor-core apply (m2l_dense.cu).
+bool dense_eligible(const m2l_ops *ops, int ntgt, int nnz);
+m2l_status dense_classify(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const int32_t *tgt_ijk,
+                          const int32_t *src_ijk, const int32_t *offsets, const int32_t *sources, DenseBuckets &d,
+                          cudaStream_t s);
+m2l_status dense_prepare(const m2l_ops *ops, int precision, cudaStream_t s);
+m2l_status launch_tc_dense(const m2l_ops *ops, const DenseBuckets &d, int precision, const float *in, void *out,
+                           int out_fp64, double scale, cudaStream_t s);
 
 // General tensor-core apply (the large-order kernel over ncls operator images
 // of vector length N <= 256; used by the directional M2L).  tc_general_config

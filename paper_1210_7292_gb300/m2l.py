@@ -73,6 +73,7 @@ def lib():
             "m2l_plan_apply": [P, P, P, I, I, P],
             "m2l_plan_query": [P, P, P, P],
             "m2l_plan_classify": [P, ctypes.POINTER(m2l_level), P],
+            "m2l_plan_kernel_info": [P, P, P, P],
             "m2l_fmm_create": [P, I, P, I, I, D, D, P, ctypes.POINTER(P)],
             "m2l_fmm_evaluate": [P, P, P, P, I, P],
             "m2l_fmm_query": [P, I, P, P, P],
@@ -374,6 +375,15 @@ def m2l_plan_query(plan: Plan):
     return counts, rec[:nvalid.value]
 
 
+def m2l_plan_kernel_info(plan: Plan):
+    """{"dense": bool, "units": int, "unit_width": int}: whether the plan's
+    tensor-core applies take the target-stationary kernel, and its unit layout."""
+    d, u, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check("m2l_plan_kernel_info", lib().m2l_plan_kernel_info(plan.handle, ctypes.byref(d), ctypes.byref(u),
+                                                              ctypes.byref(w)))
+    return {"dense": bool(d.value), "units": u.value, "unit_width": w.value}
+
+
 def m2l_apply_batch(ops_list, levels, multipoles, locals_, precision="fp32", locals_fp64=False, stream=None):
     n = len(ops_list)
     p, tin, tout = _vec_dtypes(precision, locals_fp64)
@@ -456,6 +466,7 @@ def m2l_sync_status(ops: Ops, stream=None):
 
 
 M2L_DEBUG_STALL_PRODUCER = 1
+M2L_DEBUG_NO_DENSE = 2
 
 
 def m2l_ops_set_debug(ops: Ops, flags: int):

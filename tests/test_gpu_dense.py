@@ -1,0 +1,158 @@
+"""The target-stationary tensor-core kernel (full levels, ell <= 5) against the
+oracle, through the C ABI: full and nearly full levels (domain boundary, a
+ragged last unit per octant, empty columns), the three kernels of the
+configurations, FP64 locals, accumulation into non-zero locals, the adjoint,
+agreement with the operator-bucketed kernel on the same plan, and the bounded
+wait of its failure path."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import TOL, device, gpu_ops, make_level, oracle_ops, pruned_cells
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TC = ["tf32", "bf16x3", "tf32x3"]
+
+
+@pytest.fixture(scope="module")
+def m2l():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as g
+    g.build()
+    from paper_1210_7292_gb300 import m2l as mod
+    return mod
+
+
+_ORACLE = {}
+
+
+def _oracle_level(ell, kind, level, cells, w, init=None, adjoint=False):
+    """The oracle's (adjoint) level, cached across the precisions of one case."""
+    key = (ell, kind, level, len(cells), float(w[0, 0]), adjoint)
+    if key not in _ORACLE:
+        off, src = oracle.interaction_lists(cells, cells)
+        K = oracle_ops(ell, kind, level)
+        _ORACLE[key] = (oracle.m2l_apply_adjoint(K, cells, cells, off, src, w, len(cells)) if adjoint
+                        else oracle.m2l_apply(K, cells, cells, off, src, w))
+    return _ORACLE[key] if init is None else _ORACLE[key] + init
+
+
+def _check(got, ref, prec):
+    err = oracle.rel_l2(got, ref)
+    assert err < TOL[prec], (prec, err)
+    assert np.max(np.abs(got - ref)) < 50 * TOL[prec] * np.max(np.abs(ref))
+    return err
+
+
+def _plan_apply(m2l, plan, w, prec, n_out, out_fp64=False, init=None):
+    dt = torch.float64 if out_fp64 else torch.float32
+    loc = torch.zeros(n_out, w.shape[1], dtype=dt, device=device())
+    if init is not None:
+        loc += torch.from_numpy(init).to(device(), dt)
+    m2l.m2l_plan_apply(plan, torch.from_numpy(w).to(device(), torch.float32), loc, prec, out_fp64)
+    m2l.m2l_sync_status(plan.ops)
+    return loc.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", TC)
+@pytest.mark.parametrize("ell,kind,level,keep", [(4, 0, 4, 1.0), (5, 1, 4, 0.93), (3, 2, 4, 1.0), (2, 0, 5, 0.9)])
+def test_dense_matches_oracle(m2l, prec, ell, kind, level, keep):
+    from paper_1210_7292_gb300 import synth
+    cells = synth.full_grid(level) if keep == 1.0 else pruned_cells(level, keep, seed=ell * 11 + level)
+    rng = np.random.default_rng(ell + 300)
+    w = rng.standard_normal((len(cells), ell ** 3))
+    init = rng.standard_normal((len(cells), ell ** 3))
+    lv = make_level(m2l, cells, level)
+    ops = gpu_ops(m2l, ell, kind, level)
+    plan = m2l.m2l_plan_create(ops, lv)
+    info = m2l.m2l_plan_kernel_info(plan)
+    assert info["dense"], info
+    ref = _oracle_level(ell, kind, level, cells, w, init=init)
+    err = _check(_plan_apply(m2l, plan, w, prec, len(cells), init=init), ref, prec)
+    print("dense %s ell=%d kind=%d level=%d keep=%.2f (%d cells, %d units of %d): rel L2 %.2e"
+          % (prec, ell, kind, level, keep, len(cells), info["units"], info["unit_width"], err))
+
+
+@pytest.mark.parametrize("prec", TC)
+def test_dense_fp64_locals_adjoint_and_bucketed_agree(m2l, prec):
+    """One plan applied by both tensor-core kernels (the bucketed one through
+    the M2L_DEBUG_NO_DENSE switch), FP64 locals, and the adjoint plan."""
+    from paper_1210_7292_gb300 import synth
+    ell, level = 5, 4
+    cells = synth.full_grid(level)
+    w = synth.gaussian_vectors(len(cells), ell ** 3, seed=301)
+    lv = make_level(m2l, cells, level)
+    ops = gpu_ops(m2l, ell, 0, level)
+    plan = m2l.m2l_plan_create(ops, lv)
+    adj = m2l.m2l_plan_create(ops, lv, adjoint=True)
+    assert m2l.m2l_plan_kernel_info(plan)["dense"] and m2l.m2l_plan_kernel_info(adj)["dense"]
+    ref = _oracle_level(ell, 0, level, cells, w)
+    dense = _plan_apply(m2l, plan, w, prec, len(cells), out_fp64=True)
+    _check(dense, ref, prec)
+    m2l.m2l_ops_set_debug(ops, m2l.M2L_DEBUG_NO_DENSE)
+    bucketed = _plan_apply(m2l, plan, w, prec, len(cells), out_fp64=True)
+    m2l.m2l_ops_set_debug(ops, 0)
+    _check(bucketed, ref, prec)
+    assert oracle.rel_l2(dense, bucketed) < TOL[prec]
+    ref_adj = _oracle_level(ell, 0, level, cells, w, adjoint=True)
+    _check(_plan_apply(m2l, adj, w, prec, len(cells)), ref_adj, prec)
+
+
+def test_dense_level5_sampled_and_repeatable(m2l):
+    """The benchmark's level (full level 5, ell = 5, 1/r) in BF16x3: sampled
+    targets against the oracle, and two applies bit-identical."""
+    from paper_1210_7292_gb300 import synth
+    ell, level = 5, 5
+    cells = synth.full_grid(level)
+    w = synth.gaussian_vectors(len(cells), ell ** 3, seed=302)
+    lv = make_level(m2l, cells, level)
+    ops = gpu_ops(m2l, ell, 0, level)
+    plan = m2l.m2l_plan_create(ops, lv)
+    info = m2l.m2l_plan_kernel_info(plan)
+    assert info["dense"]
+    a = _plan_apply(m2l, plan, w, "bf16x3", len(cells))
+    b = _plan_apply(m2l, plan, w, "bf16x3", len(cells))
+    assert np.array_equal(a, b)        # one write per (target, node): no order-dependent sums
+    rng = np.random.default_rng(303)
+    samp = np.unique(np.concatenate([[0, len(cells) - 1], rng.choice(len(cells), 62, replace=False)]))
+    off, src = oracle.interaction_lists(cells[samp], cells)
+    ref = oracle.m2l_apply(oracle_ops(ell, 0, level), cells[samp], cells, off, src, w)
+    err = _check(a[samp], ref, "bf16x3")
+    print("dense level 5 bf16x3 (%d units of %d): rel L2 %.2e" % (info["units"], info["unit_width"], err))
+
+
+def test_sparse_levels_keep_the_bucketed_kernel(m2l):
+    cells = pruned_cells(4, 0.4, 304)
+    lv = make_level(m2l, cells, 4)
+    plan = m2l.m2l_plan_create(gpu_ops(m2l, 4, 0, 4), lv)
+    assert not m2l.m2l_plan_kernel_info(plan)["dense"]
+
+
+def test_dense_bounded_wait_reports_timeout(m2l):
+    """The failure switch on the dense kernel: its producer withholds the first
+    stage, the MMA warp's bounded wait runs out, the kernel returns, the host
+    reads M2L_ETIMEOUT and a correct apply follows on the same context."""
+    from paper_1210_7292_gb300 import synth
+    ell, level = 4, 4
+    cells = synth.full_grid(level)
+    w = synth.gaussian_vectors(len(cells), ell ** 3, seed=305)
+    lv = make_level(m2l, cells, level)
+    ops = gpu_ops(m2l, ell, 0, level)
+    plan = m2l.m2l_plan_create(ops, lv)
+    assert m2l.m2l_plan_kernel_info(plan)["dense"]
+    m2l.m2l_ops_set_debug(ops, m2l.M2L_DEBUG_STALL_PRODUCER)
+    loc = torch.zeros(len(cells), ell ** 3, dtype=torch.float32, device=device())
+    t0 = time.time()
+    m2l.m2l_plan_apply(plan, torch.from_numpy(w).to(device(), torch.float32), loc, "bf16x3")
+    with pytest.raises(m2l.M2LError) as ei:
+        m2l.m2l_sync_status(ops)
+    assert ei.value.status == m2l.M2L_ETIMEOUT and time.time() - t0 < 30.0
+    m2l.m2l_ops_set_debug(ops, 0)
+    off, src = oracle.interaction_lists(cells, cells)
+    ref = oracle.m2l_apply(oracle_ops(ell, 0, level), cells, cells, off, src, w)
+    _check(_plan_apply(m2l, plan, w, "bf16x3", len(cells)), ref, "bf16x3")
