@@ -11,8 +11,8 @@
 // unit of up to nu target cells (columns) of one octant, every transfer
 // vector of the unit is one product D += K_t W_t, where column j of W_t is
 // the unpermuted multipole of the source X_j - t (zero if there is none);
-// the sum over the interaction list of Eq. (7) accumulates in TMEM and each
-// local is written once per launch.
+// the sum over the interaction list of Eq. (7) runs on chip and each local is
+// written once per launch.
 //
 // Classification (step a3 for this kernel): targets are ranked by the octant
 // of their cell (stable), each octant's run is split into balanced units,
@@ -27,9 +27,11 @@
 // slot's operator image into shared memory with one bulk copy and gathers
 // the nu source rows of the same K column with TMA tile::gather4 loads (4
 // rows per load, 128-byte swizzle, straight into the UMMA operand layout);
-// one thread of the MMA warp issues tcgen05.mma (M = 128, N = nu) into one
-// of two TMEM accumulators; four epilogue warps read a finished unit with
-// tcgen05.ld and add it, times w^degree, to the locals: one atomic add per
+// one thread of the MMA warp issues tcgen05.mma (M = 128, N = nu) for one
+// slot into one of two TMEM accumulators (the K sum of one transfer vector);
+// sixteen epilogue warps read each slot's product with tcgen05.ld and add it
+// into FP32 registers, and at the end of the unit add the sums, times
+// w^degree, to the locals: one atomic add per
 // (target, node) and launch.  Every wait is bounded (about two seconds); on
 // expiry the CTA records M2L_ETIMEOUT, drains its own copies and MMAs,
 // frees TMEM and returns.
@@ -364,8 +366,10 @@ __device__ __forceinline__ void tma_gather4(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-constexpr int kDenseThreads = 192;    // warp 0 TMA producer, warp 1 MMA, warps 2-5 epilogue
 constexpr int kDenseEpiWarp0 = 2;
+constexpr int kDenseEpiWarps = 16;
+constexpr int kDenseThreads = (kDenseEpiWarp0 + kDenseEpiWarps) * 32;   // TMA, MMA, 16 epilogue warps
+constexpr int kDenseGroupsPerWarp = 4;                                    // 16-column groups, nu <= 256
 constexpr int kDenseMaxStages = 4;
 constexpr int kDenseDStride = 256;    // TMEM columns between the two accumulators
 
@@ -379,7 +383,7 @@ __host__ __device__ constexpr int dense_stage_bytes(int nu)
 // One persistent CTA per SM over units blockIdx.x, blockIdx.x + gridDim.x, ...
 // Shared memory: nstages stages of [operator K column: parts x 128 rows x 128 B]
 // [gathered K column: parts x nu rows x 128 B], then the mbarriers.  TMEM: two
-// accumulators of nu columns, 256 apart.
+// accumulators of nu columns, 256 apart, alternating per (unit, slot).
 template <int KIND>
 __global__ void __launch_bounds__(kDenseThreads, 1)
 tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restrict__ a_img,
@@ -416,7 +420,7 @@ tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restr
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(dfull + i, 1);
-            mbar_init(dempty + i, 4 * 32);
+            mbar_init(dempty + i, kDenseEpiWarps * 32);
         }
         mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -481,21 +485,24 @@ tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restr
         __syncwarp();
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issue
+        // one TMEM job per (unit, slot): the K sum of one transfer vector's product
+        // accumulates in TMEM, the sum over the slots in the epilogue's registers
         if (lane == 0) {
             const uint32_t idesc = instr_desc(Tr::fmt, nu);
-            long it = 0;
-            int uc = 0;
+            long it = 0, jc = 0;
             bool issued = false, stop = false;
             for (int u = blockIdx.x; u < nunits && !stop; u += gridDim.x) {
                 const uint16_t *row = slots + (size_t)u * kSlotRow;
                 const int ns = row[0];
-                if (ns == 0) continue;
-                const int b = uc & 1;
-                if (!mbar_wait(dempty + b, ((uc >> 1) & 1) ^ 1, abort_flag, status)) break;
-                tc_fence_after();
-                const uint32_t d = tmem_base + (uint32_t)(b * kDenseDStride);
-                uint32_t accum = 0;
-                for (int si = 0; si < ns && !stop; ++si) {
+                for (int si = 0; si < ns && !stop; ++si, ++jc) {
+                    const int b = (int)(jc & 1);
+                    if (!mbar_wait(dempty + b, (uint32_t)(((jc >> 1) & 1) ^ 1), abort_flag, status)) {
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem_base + (uint32_t)(b * kDenseDStride);
+                    uint32_t accum = 0;
                     for (int ka = 0; ka < katoms; ++ka, ++it) {
                         const int s = (int)(it % nstages);
                         if (!mbar_wait(full + s, (uint32_t)((it / nstages) & 1), abort_flag, status)) {
@@ -519,10 +526,9 @@ tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restr
                         umma_commit(empty + s);
                         issued = true;
                     }
+                    if (stop) break;
+                    umma_commit(dfull + b);
                 }
-                if (stop) break;
-                umma_commit(dfull + b);
-                ++uc;
             }
             if (issued) {
                 // every MMA issued by this thread has completed before TMEM is freed
@@ -533,33 +539,61 @@ tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restr
         __syncwarp();
     } else {
         // ---------------------------------------------------------- epilogue
-        const int q = warp & 3;                // TMEM lane quarter of this warp
-        const int node = 32 * q + lane;        // accumulator row = local node index
-        int uc = 0;
-        for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+        // 16 warps: four per TMEM lane quarter, warp `sub` of a quarter owning the
+        // 16-column groups sub, sub + 4, sub + 8, sub + 12 of the accumulator.
+        // Each slot's product is added into FP32 registers (round to nearest),
+        // so a unit's locals are the register sums over its slots.
+        const int q = warp & 3;                         // TMEM lane quarter of this warp
+        const int sub = (warp - kDenseEpiWarp0) >> 2;   // 0..3
+        const int node = 32 * q + lane;                 // accumulator row = local node index
+        const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
+        long jc = 0;
+        bool stop = false;
+        for (int u = blockIdx.x; u < nunits && !stop; u += gridDim.x) {
             const int ns = slots[(size_t)u * kSlotRow];
             if (ns == 0) continue;
-            const int b = uc & 1;
-            const bool ok = mbar_wait(dfull + b, (uint32_t)((uc >> 1) & 1), abort_flag, status);
-            if (!__all_sync(0xffffffffu, ok)) break;   // tcgen05.ld below is warp-collective
-            tc_fence_after();
+            float acc[kDenseGroupsPerWarp][16];
+#pragma unroll
+            for (int gi = 0; gi < kDenseGroupsPerWarp; ++gi)
+#pragma unroll
+                for (int c = 0; c < 16; ++c) acc[gi][c] = 0.0f;
+            for (int si = 0; si < ns; ++si, ++jc) {
+                const int b = (int)(jc & 1);
+                const bool ok = mbar_wait(dfull + b, (uint32_t)((jc >> 1) & 1), abort_flag, status);
+                if (!__all_sync(0xffffffffu, ok)) {   // tcgen05.ld below is warp-collective
+                    stop = true;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int gi = 0; gi < kDenseGroupsPerWarp; ++gi) {
+                    const int c0 = 16 * (sub + 4 * gi);
+                    if (c0 < nu) {
+                        float v[16];
+                        tmem_ld<16>(lane_base + (uint32_t)(b * kDenseDStride + c0), v);
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) acc[gi][c] += v[c];
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(dempty + b);
+            }
+            if (stop) break;
             const int32_t *tg = unit_tgt + (size_t)u * nu;
-            for (int c0 = 0; c0 < nu; c0 += 16) {
-                float v[16];
-                tmem_ld<16>(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kDenseDStride + c0), v);
+#pragma unroll
+            for (int gi = 0; gi < kDenseGroupsPerWarp; ++gi) {
+                const int c0 = 16 * (sub + 4 * gi);
+                if (c0 >= nu) continue;
                 const int tl = tg[c0 + (lane & 15)];
 #pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                    const int t = __shfl_sync(0xffffffffu, tl, jj);
+                for (int c = 0; c < 16; ++c) {
+                    const int t = __shfl_sync(0xffffffffu, tl, c);
                     if (t >= 0 && node < n3) {
-                        if (out_f64) atomicAdd(out_f64 + (size_t)t * n3 + node, (double)v[jj] * (double)scale);
-                        else atomicAdd(out_f32 + (size_t)t * n3 + node, v[jj] * scale);
+                        if (out_f64) atomicAdd(out_f64 + (size_t)t * n3 + node, (double)acc[gi][c] * (double)scale);
+                        else atomicAdd(out_f32 + (size_t)t * n3 + node, acc[gi][c] * scale);
                     }
                 }
             }
-            tc_fence_before();
-            mbar_arrive(dempty + b);
-            ++uc;
         }
     }
     tc_fence_before();
