@@ -370,6 +370,7 @@ constexpr int kDenseEpiWarp0 = 2;
 constexpr int kDenseEpiWarps = 16;
 constexpr int kDenseThreads = (kDenseEpiWarp0 + kDenseEpiWarps) * 32;   // TMA, MMA, 16 epilogue warps
 constexpr int kDenseGroupsPerWarp = 4;                                    // 16-column groups, nu <= 256
+constexpr int kSlotRegs = (kSlots + 31) / 32;                             // slot list entries per lane
 constexpr int kDenseMaxStages = 4;
 constexpr int kDenseDStride = 256;    // TMEM columns between the two accumulators
 
@@ -439,15 +440,42 @@ tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restr
 
     if (warp == 0) {
         // ---------------------------------------------------------- TMA producer
+        // Lane l gathers the column groups l and l + 32 (4 columns each) of every
+        // part.  The slot list of a unit is held in registers (lane l: entries
+        // l, l + 32, ...), and the source indices of the next slot are loaded
+        // while the current one is issued, so no gather waits on a table load.
         long it = 0;
         unsigned issued = 0, parity = 0;   // per stage: a fill is outstanding or done; its phase parity
         bool stop = false;
+        const int4 zero4 = make_int4(0, 0, 0, 0);
         for (int u = blockIdx.x; u < nunits && !stop; u += gridDim.x) {
             const uint16_t *row = slots + (size_t)u * kSlotRow;
             const int ns = row[0];
+            if (ns == 0) continue;
+            int sl[kSlotRegs];
+#pragma unroll
+            for (int r = 0; r < kSlotRegs; ++r) sl[r] = (32 * r + lane < ns) ? row[1 + 32 * r + lane] : 0;
+            const int32_t *utab = tab + (size_t)u * kSlots * nu;
+            auto slot_of = [&](int si) {
+                int v = 0;
+#pragma unroll
+                for (int r = 0; r < kSlotRegs; ++r) {
+                    const int x = __shfl_sync(0xffffffffu, sl[r], si & 31);
+                    if ((si >> 5) == r) v = x;
+                }
+                return v;
+            };
+            auto load_cols = [&](int slot, int4 (&v)[2]) {
+                const int4 *t4 = reinterpret_cast<const int4 *>(utab + (size_t)slot * nu);
+                v[0] = (lane < ngrp) ? __ldg(t4 + lane) : zero4;
+                v[1] = (lane + 32 < ngrp) ? __ldg(t4 + lane + 32) : zero4;
+            };
+            int slot = slot_of(0);
+            int4 cur[2], nxt[2];
+            load_cols(slot, cur);
             for (int si = 0; si < ns && !stop; ++si) {
-                const int slot = row[1 + si];
-                const int4 *tab4 = reinterpret_cast<const int4 *>(tab + ((size_t)u * kSlots + slot) * nu);
+                const int slot_next = (si + 1 < ns) ? slot_of(si + 1) : slot;
+                if (si + 1 < ns) load_cols(slot_next, nxt);
                 for (int ka = 0; ka < katoms; ++ka, ++it) {
                     const int s = (int)(it % nstages);
                     const uint32_t ph = (uint32_t)((it / nstages) & 1);
@@ -466,16 +494,25 @@ tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restr
                         bulk_g2s(st, a_img + ((size_t)slot * katoms + ka) * A_BYTES, A_BYTES, full + s);
                     }
                     __syncwarp();
-                    for (int q = lane; q < ngrp * Tr::nparts; q += 32) {
-                        const int part = q / ngrp, grp = q - part * ngrp;
-                        const int4 v = __ldg(tab4 + grp);
-                        tma_gather4(st + A_BYTES + part * b_part + grp * 512, &bmap, part * kpad + ka * E,
-                                    v.x ? v.x - 1 : nsrc, v.y ? v.y - 1 : nsrc, v.z ? v.z - 1 : nsrc,
-                                    v.w ? v.w - 1 : nsrc, full + s);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int grp = lane + 32 * h;
+                        if (grp < ngrp) {
+                            const int4 v = cur[h];
+                            const int y0 = v.x ? v.x - 1 : nsrc, y1 = v.y ? v.y - 1 : nsrc;
+                            const int y2 = v.z ? v.z - 1 : nsrc, y3 = v.w ? v.w - 1 : nsrc;
+#pragma unroll
+                            for (int part = 0; part < Tr::nparts; ++part)
+                                tma_gather4(st + A_BYTES + part * b_part + grp * 512, &bmap, part * kpad + ka * E,
+                                            y0, y1, y2, y3, full + s);
+                        }
                     }
                     issued |= 1u << s;
                     parity = (parity & ~(1u << s)) | (ph << s);
                 }
+                slot = slot_next;
+                cur[0] = nxt[0];
+                cur[1] = nxt[1];
             }
         }
         // every copy this CTA issued lands before its shared memory is released
@@ -631,11 +668,6 @@ m2l_status encode_fn(EncodeTiled *out)
     *out = fn;
     return M2L_OK;
 }
-
-template <int KIND> struct DensePrec;
-template <> struct DensePrec<TC_TF32> { static constexpr int value = M2L_TF32; };
-template <> struct DensePrec<TC_BF16X3> { static constexpr int value = M2L_BF16X3; };
-template <> struct DensePrec<TC_TF32X3> { static constexpr int value = M2L_TF32X3; };
 
 Layout &dense_layout(const m2l_ops *ops, int kind)
 {
