@@ -366,9 +366,11 @@ __device__ __forceinline__ void tma_gather4(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-constexpr int kDenseEpiWarp0 = 2;
+constexpr int kDenseProdWarps = 4;                                        // warps 0-3: TMA producers
+constexpr int kDenseMmaWarp = 4;
+constexpr int kDenseEpiWarp0 = 5;
 constexpr int kDenseEpiWarps = 16;
-constexpr int kDenseThreads = (kDenseEpiWarp0 + kDenseEpiWarps) * 32;   // TMA, MMA, 16 epilogue warps
+constexpr int kDenseThreads = (kDenseEpiWarp0 + kDenseEpiWarps) * 32;
 constexpr int kDenseGroupsPerWarp = 4;                                    // 16-column groups, nu <= 256
 constexpr int kSlotRegs = (kSlots + 31) / 32;                             // slot list entries per lane
 constexpr int kDenseMaxStages = 4;
@@ -382,6 +384,7 @@ __host__ __device__ constexpr int dense_stage_bytes(int nu)
 }
 
 // One persistent CTA per SM over units blockIdx.x, blockIdx.x + gridDim.x, ...
+// Warps 0-3 TMA producers, warp 4 MMA, warps 5-20 epilogue.
 // Shared memory: nstages stages of [operator K column: parts x 128 rows x 128 B]
 // [gathered K column: parts x nu rows x 128 B], then the mbarriers.  TMEM: two
 // accumulators of nu columns, 256 apart, alternating per (unit, slot).
@@ -426,7 +429,7 @@ tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restr
         mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {
+    if (warp == kDenseMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem_base)),
                      "r"(512)
                      : "memory");
@@ -438,16 +441,20 @@ tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restr
     const uint32_t tmem_base = s_tmem_base;
     volatile int *abort_flag = &s_abort;
 
-    if (warp == 0) {
-        // ---------------------------------------------------------- TMA producer
-        // Lane l gathers the column groups l and l + 32 (4 columns each) of every
-        // part.  The slot list of a unit is held in registers (lane l: entries
-        // l, l + 32, ...), and the source indices of the next slot are loaded
-        // while the current one is issued, so no gather waits on a table load.
+    if (warp < kDenseProdWarps) {
+        // ---------------------------------------------------------- TMA producers
+        // Gather task 32 w + lane of warp w is (part, column group) = (task / ngrp,
+        // task % ngrp): one tile::gather4 per lane and stage.  Warp 0 also posts
+        // the stage's expected bytes and copies the operator's K column.  The
+        // slot list of a unit is held in registers (lane l: entries l, l + 32,
+        // ...), and the source indices of the next slot are loaded while the
+        // current one is issued, so no gather waits on a table load.
+        const int task = 32 * warp + lane;
+        const bool has_task = task < ngrp * Tr::nparts;
+        const int part = has_task ? task / ngrp : 0, grp = has_task ? task - part * ngrp : 0;
         long it = 0;
         unsigned issued = 0, parity = 0;   // per stage: a fill is outstanding or done; its phase parity
         bool stop = false;
-        const int4 zero4 = make_int4(0, 0, 0, 0);
         for (int u = blockIdx.x; u < nunits && !stop; u += gridDim.x) {
             const uint16_t *row = slots + (size_t)u * kSlotRow;
             const int ns = row[0];
@@ -465,17 +472,15 @@ tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restr
                 }
                 return v;
             };
-            auto load_cols = [&](int slot, int4 (&v)[2]) {
-                const int4 *t4 = reinterpret_cast<const int4 *>(utab + (size_t)slot * nu);
-                v[0] = (lane < ngrp) ? __ldg(t4 + lane) : zero4;
-                v[1] = (lane + 32 < ngrp) ? __ldg(t4 + lane + 32) : zero4;
+            auto load_cols = [&](int slot) {
+                return has_task ? __ldg(reinterpret_cast<const int4 *>(utab + (size_t)slot * nu) + grp)
+                                : make_int4(0, 0, 0, 0);
             };
             int slot = slot_of(0);
-            int4 cur[2], nxt[2];
-            load_cols(slot, cur);
+            int4 cur = load_cols(slot);
             for (int si = 0; si < ns && !stop; ++si) {
                 const int slot_next = (si + 1 < ns) ? slot_of(si + 1) : slot;
-                if (si + 1 < ns) load_cols(slot_next, nxt);
+                const int4 nxt = load_cols(slot_next);
                 for (int ka = 0; ka < katoms; ++ka, ++it) {
                     const int s = (int)(it % nstages);
                     const uint32_t ph = (uint32_t)((it / nstages) & 1);
@@ -489,30 +494,19 @@ tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restr
                     // test switch: withholding the first stage makes the MMA warp's wait run out
                     if (stall_first_stage && it == 0) continue;
                     uint8_t *st = smem + (size_t)s * stage_bytes;
-                    if (lane == 0) {
+                    if (warp == 0 && lane == 0) {
                         mbar_arrive_expect_tx(full + s, (uint32_t)stage_bytes);
                         bulk_g2s(st, a_img + ((size_t)slot * katoms + ka) * A_BYTES, A_BYTES, full + s);
                     }
-                    __syncwarp();
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int grp = lane + 32 * h;
-                        if (grp < ngrp) {
-                            const int4 v = cur[h];
-                            const int y0 = v.x ? v.x - 1 : nsrc, y1 = v.y ? v.y - 1 : nsrc;
-                            const int y2 = v.z ? v.z - 1 : nsrc, y3 = v.w ? v.w - 1 : nsrc;
-#pragma unroll
-                            for (int part = 0; part < Tr::nparts; ++part)
-                                tma_gather4(st + A_BYTES + part * b_part + grp * 512, &bmap, part * kpad + ka * E,
-                                            y0, y1, y2, y3, full + s);
-                        }
-                    }
+                    if (has_task)
+                        tma_gather4(st + A_BYTES + part * b_part + grp * 512, &bmap, part * kpad + ka * E,
+                                    cur.x ? cur.x - 1 : nsrc, cur.y ? cur.y - 1 : nsrc, cur.z ? cur.z - 1 : nsrc,
+                                    cur.w ? cur.w - 1 : nsrc, full + s);
                     issued |= 1u << s;
                     parity = (parity & ~(1u << s)) | (ph << s);
                 }
                 slot = slot_next;
-                cur[0] = nxt[0];
-                cur[1] = nxt[1];
+                cur = nxt;
             }
         }
         // every copy this CTA issued lands before its shared memory is released
@@ -520,7 +514,7 @@ tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restr
             for (int s = 0; s < nstages; ++s)
                 if (issued & (1u << s)) mbar_wait_drain(full + s, (parity >> s) & 1u, status);
         __syncwarp();
-    } else if (warp == 1) {
+    } else if (warp == kDenseMmaWarp) {
         // ---------------------------------------------------------- MMA issue
         // one TMEM job per (unit, slot): the K sum of one transfer vector's product
         // accumulates in TMEM, the sum over the slots in the epilogue's registers
@@ -636,7 +630,7 @@ tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restr
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 1)
+    if (warp == kDenseMmaWarp)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512) : "memory");
 }
 
