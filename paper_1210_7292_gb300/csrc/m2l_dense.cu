@@ -23,10 +23,10 @@
 // Apply: the multipoles are first split once per call (hi/lo parts of
 // BF16x3 / TF32x3, the TF32 rounding of TF32) into rows of [parts][kpad]
 // plus one zero row.  One persistent CTA per SM walks its units; per unit
-// and active slot, a producer warp brings each 128-byte K column of the
-// slot's operator image into shared memory with one bulk copy and gathers
-// the nu source rows of the same K column with TMA tile::gather4 loads (4
-// rows per load, 128-byte swizzle, straight into the UMMA operand layout);
+// and active slot, one producer thread brings each 128-byte K column of the
+// slot's operator image into shared memory with one bulk copy, and 128
+// producer threads copy the nu source rows of the same K column with 16-byte
+// cp.async copies, straight into the 128-byte-swizzled UMMA operand layout;
 // one thread of the MMA warp issues tcgen05.mma (M = 128, N = nu) for one
 // slot into one of two TMEM accumulators (the K sum of one transfer vector);
 // sixteen epilogue warps read each slot's product with tcgen05.ld and add it
@@ -35,10 +35,6 @@
 // (target, node) and launch.  Every wait is bounded (about two seconds); on
 // expiry the CTA records M2L_ETIMEOUT, drains its own copies and MMAs,
 // frees TMEM and returns.
-#include <cuda.h>
-
-#include <mutex>
-
 #include "m2l_tcgen05.cuh"
 
 namespace m2l {
@@ -325,7 +321,7 @@ __global__ void dense_image_kernel(int n3, int katoms, const double *__restrict_
     }
 }
 
-// The multipoles as TMA-gatherable rows: row y = [part][kpad] of the split
+// The multipoles as copyable rows: row y = [part][kpad] of the split
 // values of multipole y (hi = round(x), lo = round(x - hi) for the split
 // precisions, the TF32 rounding for TF32), zero-padded; row nsrc is zero.
 template <int KIND>
@@ -353,26 +349,24 @@ __global__ void dense_split_kernel(int nsrc, int n3, int kpad, const float *__re
     }
 }
 
-// tile::gather4: four rows (y0..y3) of the box [x, x + 128 bytes) of a 2-D
-// tensor into four consecutive 128-byte rows of shared memory at dst, with
-// the tensor map's 128-byte swizzle; completion counted on bar.
-__device__ __forceinline__ void tma_gather4(void *dst, const CUtensorMap *map, int x, int y0, int y1, int y2, int y3,
-                                            uint64_t *bar)
+// 16-byte global -> shared copy through L2 (cp.async), and an arrive on bar
+// that fires once all of this thread's earlier cp.async copies have landed.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
 {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y0), "r"(y1), "r"(y2), "r"(y3), "r"(smem_u32(bar))
-        : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t *bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-constexpr int kDenseProdWarps = 4;                                        // warps 0-3: TMA producers
+constexpr int kDenseProdWarps = 4;                                        // warps 0-3: producers
 constexpr int kDenseMmaWarp = 4;
 constexpr int kDenseEpiWarp0 = 5;
 constexpr int kDenseEpiWarps = 16;
 constexpr int kDenseThreads = (kDenseEpiWarp0 + kDenseEpiWarps) * 32;
 constexpr int kDenseGroupsPerWarp = 4;                                    // 16-column groups, nu <= 256
-constexpr int kSlotRegs = (kSlots + 31) / 32;                             // slot list entries per lane
+constexpr int kDenseMaxColM = 16;                                         // panel columns per producer thread (nu <= 256)
 constexpr int kDenseMaxStages = 4;
 constexpr int kDenseDStride = 256;    // TMEM columns between the two accumulators
 
@@ -384,13 +378,10 @@ __host__ __device__ constexpr int dense_stage_bytes(int nu)
 }
 
 // One persistent CTA per SM over units blockIdx.x, blockIdx.x + gridDim.x, ...
-// Warps 0-3 TMA producers, warp 4 MMA, warps 5-20 epilogue.
-// Shared memory: nstages stages of [operator K column: parts x 128 rows x 128 B]
-// [gathered K column: parts x nu rows x 128 B], then the mbarriers.  TMEM: two
-// accumulators of nu columns, 256 apart, alternating per (unit, slot).
+// Warps 0-3 producers, warp 4 MMA, warps 5-20 epilogue.
 template <int KIND>
 __global__ void __launch_bounds__(kDenseThreads, 1)
-tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restrict__ a_img,
+tc_dense_kernel(const uint8_t *__restrict__ bsplit, const uint8_t *__restrict__ a_img,
                 const int32_t *__restrict__ meta, const uint16_t *__restrict__ slots, const int32_t *__restrict__ tab,
                 const int32_t *__restrict__ unit_tgt, int nu, int katoms, int nstages, int nsrc, int n3,
                 float *__restrict__ out_f32, double *__restrict__ out_f64, float scale, int *status,
@@ -404,13 +395,12 @@ tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restr
     const int b_part = nu * 128;                   // one part of a gathered K column
     const int stage_bytes = A_BYTES + Tr::nparts * b_part;
     const int kpad = katoms * E;
-    const int ngrp = nu / 4;                       // gather4 loads per part
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)nstages * stage_bytes);
-    uint64_t *full = bars, *empty = bars + kDenseMaxStages, *dfull = bars + 2 * kDenseMaxStages;
-    uint64_t *dempty = dfull + 2, *drain = dempty + 2;
+    uint64_t *afull = bars, *bfull = bars + kDenseMaxStages, *empty = bars + 2 * kDenseMaxStages;
+    uint64_t *dfull = bars + 3 * kDenseMaxStages, *dempty = dfull + 2, *drain = dempty + 2;
     __shared__ uint32_t s_tmem_base;
     __shared__ int s_abort;
 
@@ -419,7 +409,8 @@ tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restr
     if (threadIdx.x == 0) {
         s_abort = 0;
         for (int i = 0; i < nstages; ++i) {
-            mbar_init(full + i, 1);
+            mbar_init(afull + i, 1);
+            mbar_init(bfull + i, kDenseProdWarps * 32);
             mbar_init(empty + i, 1);
         }
         for (int i = 0; i < 2; ++i) {
@@ -442,45 +433,42 @@ tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restr
     volatile int *abort_flag = &s_abort;
 
     if (warp < kDenseProdWarps) {
-        // ---------------------------------------------------------- TMA producers
-        // Gather task 32 w + lane of warp w is (part, column group) = (task / ngrp,
-        // task % ngrp): one tile::gather4 per lane and stage.  Warp 0 also posts
-        // the stage's expected bytes and copies the operator's K column.  The
-        // slot list of a unit is held in registers (lane l: entries l, l + 32,
-        // ...), and the source indices of the next slot are loaded while the
-        // current one is issued, so no gather waits on a table load.
-        const int task = 32 * warp + lane;
-        const bool has_task = task < ngrp * Tr::nparts;
-        const int part = has_task ? task / ngrp : 0, grp = has_task ? task - part * ngrp : 0;
+        // ---------------------------------------------------------- producers
+        // Thread t of the 128 copies, per stage, the 16-byte chunk t % 8 of the
+        // 128-byte K column of columns t / 8 + 16 m (every part) from the split
+        // multipole rows straight to its 128-byte-swizzled place in the operand
+        // panel (cp.async through L2), then arms the stage's panel barrier with
+        // an arrive that fires when its copies have landed.  Thread 0 also copies
+        // the stage's operator K column (one bulk copy on its own barrier).
+        // Slot numbers are read two slots ahead and source rows one slot ahead.
+        const int pt = threadIdx.x;
+        const int cb = pt >> 3, kc = pt & 7;
+        const int ncm = nu >> 4;                  // columns of this thread
+        const size_t row_bytes = (size_t)Tr::nparts * kpad * Tr::esz;
+        const uint8_t *src_base = bsplit + kc * 16;
         long it = 0;
-        unsigned issued = 0, parity = 0;   // per stage: a fill is outstanding or done; its phase parity
+        unsigned issued = 0, parity = 0;          // thread 0: operator copies per stage and their phase
         bool stop = false;
         for (int u = blockIdx.x; u < nunits && !stop; u += gridDim.x) {
-            const uint16_t *row = slots + (size_t)u * kSlotRow;
-            const int ns = row[0];
+            const uint16_t *row = slots + (size_t)u * kSlotRow + 1;
+            const int ns = row[-1];
             if (ns == 0) continue;
-            int sl[kSlotRegs];
+            const int32_t *utab = tab + (size_t)u * kSlots * nu + cb;
+            int y[kDenseMaxColM], yn[kDenseMaxColM];
+            auto rows_of = [&](int slot, int (&v)[kDenseMaxColM]) {
+                const int32_t *t = utab + (size_t)slot * nu;
 #pragma unroll
-            for (int r = 0; r < kSlotRegs; ++r) sl[r] = (32 * r + lane < ns) ? row[1 + 32 * r + lane] : 0;
-            const int32_t *utab = tab + (size_t)u * kSlots * nu;
-            auto slot_of = [&](int si) {
-                int v = 0;
-#pragma unroll
-                for (int r = 0; r < kSlotRegs; ++r) {
-                    const int x = __shfl_sync(0xffffffffu, sl[r], si & 31);
-                    if ((si >> 5) == r) v = x;
+                for (int m = 0; m < kDenseMaxColM; ++m) {
+                    const int e = (m < ncm) ? __ldg(t + 16 * m) : 0;
+                    v[m] = e ? e - 1 : nsrc;
                 }
-                return v;
             };
-            auto load_cols = [&](int slot) {
-                return has_task ? __ldg(reinterpret_cast<const int4 *>(utab + (size_t)slot * nu) + grp)
-                                : make_int4(0, 0, 0, 0);
-            };
-            int slot = slot_of(0);
-            int4 cur = load_cols(slot);
+            int slot = row[0];
+            int slot1 = ns > 1 ? (int)row[1] : slot;
+            rows_of(slot, y);
             for (int si = 0; si < ns && !stop; ++si) {
-                const int slot_next = (si + 1 < ns) ? slot_of(si + 1) : slot;
-                const int4 nxt = load_cols(slot_next);
+                const int slot2 = (si + 2 < ns) ? (int)row[si + 2] : slot1;
+                if (si + 1 < ns) rows_of(slot1, yn);
                 for (int ka = 0; ka < katoms; ++ka, ++it) {
                     const int s = (int)(it % nstages);
                     const uint32_t ph = (uint32_t)((it / nstages) & 1);
@@ -494,25 +482,38 @@ tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restr
                     // test switch: withholding the first stage makes the MMA warp's wait run out
                     if (stall_first_stage && it == 0) continue;
                     uint8_t *st = smem + (size_t)s * stage_bytes;
-                    if (warp == 0 && lane == 0) {
-                        mbar_arrive_expect_tx(full + s, (uint32_t)stage_bytes);
-                        bulk_g2s(st, a_img + ((size_t)slot * katoms + ka) * A_BYTES, A_BYTES, full + s);
+                    if (pt == 0) {
+                        mbar_arrive_expect_tx(afull + s, (uint32_t)A_BYTES);
+                        bulk_g2s(st, a_img + ((size_t)slot * katoms + ka) * A_BYTES, A_BYTES, afull + s);
+                        issued |= 1u << s;
+                        parity = (parity & ~(1u << s)) | (ph << s);
                     }
-                    if (has_task)
-                        tma_gather4(st + A_BYTES + part * b_part + grp * 512, &bmap, part * kpad + ka * E,
-                                    cur.x ? cur.x - 1 : nsrc, cur.y ? cur.y - 1 : nsrc, cur.z ? cur.z - 1 : nsrc,
-                                    cur.w ? cur.w - 1 : nsrc, full + s);
-                    issued |= 1u << s;
-                    parity = (parity & ~(1u << s)) | (ph << s);
+                    const uint8_t *src_k = src_base + ka * 128;
+                    uint8_t *dst_b = st + A_BYTES;
+#pragma unroll
+                    for (int m = 0; m < kDenseMaxColM; ++m) {
+                        if (m < ncm) {
+                            const int c = cb + 16 * m;
+                            const uint32_t off = (uint32_t)((c >> 3) * 1024 + (c & 7) * 128 + ((kc ^ (c & 7)) << 4));
+                            const uint8_t *src = src_k + (size_t)y[m] * row_bytes;
+#pragma unroll
+                            for (int part = 0; part < Tr::nparts; ++part)
+                                cp_async16(dst_b + part * b_part + off, src + (size_t)part * kpad * Tr::esz);
+                        }
+                    }
+                    cp_async_arrive_noinc(bfull + s);
                 }
-                slot = slot_next;
-                cur = nxt;
+                slot = slot1;
+                slot1 = slot2;
+#pragma unroll
+                for (int m = 0; m < kDenseMaxColM; ++m) y[m] = yn[m];
             }
         }
         // every copy this CTA issued lands before its shared memory is released
-        if (lane == 0)
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        if (pt == 0)
             for (int s = 0; s < nstages; ++s)
-                if (issued & (1u << s)) mbar_wait_drain(full + s, (parity >> s) & 1u, status);
+                if (issued & (1u << s)) mbar_wait_drain(afull + s, (parity >> s) & 1u, status);
         __syncwarp();
     } else if (warp == kDenseMmaWarp) {
         // ---------------------------------------------------------- MMA issue
@@ -536,10 +537,14 @@ tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restr
                     uint32_t accum = 0;
                     for (int ka = 0; ka < katoms; ++ka, ++it) {
                         const int s = (int)(it % nstages);
-                        if (!mbar_wait(full + s, (uint32_t)((it / nstages) & 1), abort_flag, status)) {
+                        const uint32_t ph = (uint32_t)((it / nstages) & 1);
+                        if (!mbar_wait(afull + s, ph, abort_flag, status) || !mbar_wait(bfull + s, ph, abort_flag, status)) {
                             stop = true;
                             break;
                         }
+                        // the panel was written by cp.async (generic proxy); the MMA reads it
+                        // through the async proxy
+                        fence_proxy_async();
                         tc_fence_after();
                         const uint32_t sa = smem_u32(smem + (size_t)s * stage_bytes);
                         const uint32_t sb = sa + (uint32_t)A_BYTES;
@@ -568,7 +573,7 @@ tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restr
             }
         }
         __syncwarp();
-    } else {
+    } else if (warp >= kDenseEpiWarp0) {
         // ---------------------------------------------------------- epilogue
         // 16 warps: four per TMEM lane quarter, warp `sub` of a quarter owning the
         // 16-column groups sub, sub + 4, sub + 8, sub + 12 of the accumulator.
@@ -639,30 +644,6 @@ tc_dense_kernel(const __grid_constant__ CUtensorMap bmap, const uint8_t *__restr
 // ---------------------------------------------------------------- host side
 namespace {
 
-using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point (the library
-// links only the CUDA runtime).
-m2l_status encode_fn(EncodeTiled *out)
-{
-    static std::once_flag once;
-    static EncodeTiled fn = nullptr;
-    static cudaError_t err = cudaSuccess;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        err = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
-        if (err == cudaSuccess && q != cudaDriverEntryPointSuccess) err = cudaErrorSymbolNotFound;
-        fn = reinterpret_cast<EncodeTiled>(p);
-    });
-    if (err != cudaSuccess || !fn) return cuda_fail(err != cudaSuccess ? err : cudaErrorSymbolNotFound,
-                                                    "cuTensorMapEncodeTiled entry point");
-    *out = fn;
-    return M2L_OK;
-}
-
 Layout &dense_layout(const m2l_ops *ops, int kind)
 {
     m2l_ops *o = const_cast<m2l_ops *>(ops);
@@ -706,21 +687,6 @@ m2l_status launch_dense_kind(const m2l_ops *ops, const DenseBuckets &d, const fl
     dense_split_kernel<KIND><<<sblocks, 256, 0, s>>>(d.nsrc, n3, kpad, in, d.bsplit.as<uint8_t>());
     M2L_LAUNCH_CHECK("dense_split_kernel");
 
-    EncodeTiled encode = nullptr;
-    if ((st = encode_fn(&encode)) != M2L_OK) return st;
-    alignas(64) CUtensorMap map;
-    const cuuint64_t gdim[2] = {(cuuint64_t)Tr::nparts * kpad, (cuuint64_t)d.nsrc + 1};
-    const cuuint64_t gstride[1] = {(cuuint64_t)row_bytes};
-    const cuuint32_t box[2] = {(cuuint32_t)(128 / Tr::esz), 1};
-    const cuuint32_t estride[2] = {1, 1};
-    const CUresult r = encode(&map, Tr::esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                              d.bsplit.p, gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
-        return M2L_ECUDA;
-    }
     const int stage = dense_stage_bytes<KIND>(d.nu);
     const int budget = max_smem_optin() - 1024 - 256;
     int nst = budget / stage;
@@ -737,7 +703,7 @@ m2l_status launch_dense_kind(const m2l_ops *ops, const DenseBuckets &d, const fl
     int grid = num_sms();
     if (grid > d.umax) grid = d.umax;
     const Layout &L = dense_layout(ops, KIND);
-    kern<<<grid, kDenseThreads, smem, s>>>(map, L.a.as<uint8_t>(), d.meta.as<int32_t>(), d.slots.as<uint16_t>(),
+    kern<<<grid, kDenseThreads, smem, s>>>(d.bsplit.as<uint8_t>(), L.a.as<uint8_t>(), d.meta.as<int32_t>(), d.slots.as<uint16_t>(),
                                           d.tab.as<int32_t>(), d.unit_tgt.as<int32_t>(), d.nu, katoms, nst, d.nsrc,
                                           n3, out_fp64 ? nullptr : (float *)out, out_fp64 ? (double *)out : nullptr,
                                           (float)scale, ops->d_status,
