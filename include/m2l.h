@@ -222,7 +222,7 @@ m2l_status m2l_plan_query(const m2l_plan *plan, int64_t *counts16, int32_t *reco
 void m2l_plan_free(m2l_plan *plan);
 /* Which kernel the tensor-core applies of a plan take.  *dense = 1 when the
  * level was also classified for the target-stationary kernel (ell <= 5,
- * full-rank operators, at least 2048 target cells whose lists hold at least
+ * full-rank operators, at least 16384 target cells whose lists hold at least
  * half of the 189 far-field entries per cell of a full level, Sec. 3.2): its
  * targets are grouped by octant into at most *units units of *unit_width
  * columns.  *dense = 0: the operator-bucketed kernel.  Host-side only (no

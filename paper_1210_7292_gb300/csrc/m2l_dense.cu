@@ -42,7 +42,7 @@ namespace {
 
 constexpr int kSlots = 343;           // transfer-vector slots, |t_i| <= 3
 constexpr int kSlotRow = 344;         // per unit: count, then up to 343 slots
-constexpr int kDenseMinTargets = 2048;
+constexpr int kDenseMinTargets = 16384;   // 8 octants x 2048: units of >= 128 columns on 152 SMs
 constexpr int kRankBlock = 256;       // targets per block of the octant ranking
 
 // ---------------------------------------------------------------- classification
@@ -190,7 +190,9 @@ bool dense_eligible(const m2l_ops *ops, int ntgt, int nnz)
 {
     // 189 far-field transfer vectors per target cell in a full level (Sec. 3.2):
     // the kernel pays for every (target, active t) column, so it takes levels
-    // whose lists are at least half full and large enough to fill the GPU
+    // whose lists are at least half full; each operator K column it streams is
+    // shared by a unit's columns, so it takes levels large enough for units of
+    // at least 128 columns on every SM
     return ops->eps <= 0.0 && ops->n3 <= 128 && ntgt >= kDenseMinTargets && (double)nnz >= 0.5 * 189.0 * ntgt;
 }
 
@@ -202,7 +204,7 @@ static int choose_nu(int ntgt)
     const long per_oct = (ntgt + 7) / 8;
     int best = 256;
     long best_cost = -1;
-    for (int nu = 256; nu >= 32; nu -= 16) {
+    for (int nu = 256; nu >= 128; nu -= 16) {
         const long units = 8 * ((per_oct + nu - 1) / nu);
         const long rounds = (units + nsm - 1) / nsm;
         const long cost = rounds * (nu + 64);

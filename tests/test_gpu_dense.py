@@ -1,6 +1,7 @@
-"""The target-stationary tensor-core kernel (full levels, ell <= 5) against the
-oracle, through the C ABI: full and nearly full levels (domain boundary, a
-ragged last unit per octant, empty columns), the three kernels of the
+"""The target-stationary tensor-core kernel (full levels of at least 16384
+cells, ell <= 5) against the oracle, through the C ABI: full and nearly full
+levels 5 and 6 (domain boundary, a ragged last unit per octant, empty
+columns), the three kernels of the
 configurations, FP64 locals, accumulation into non-zero locals, the adjoint,
 agreement with the operator-bucketed kernel on the same plan, and the bounded
 wait of its failure path."""
@@ -29,13 +30,21 @@ def m2l():
 
 
 _ORACLE = {}
+_LISTS = {}
+
+
+def _lists(cells):
+    key = (len(cells), cells.tobytes().__hash__())
+    if key not in _LISTS:
+        _LISTS[key] = oracle.interaction_lists(cells, cells)
+    return _LISTS[key]
 
 
 def _oracle_level(ell, kind, level, cells, w, init=None, adjoint=False):
     """The oracle's (adjoint) level, cached across the precisions of one case."""
     key = (ell, kind, level, len(cells), float(w[0, 0]), adjoint)
     if key not in _ORACLE:
-        off, src = oracle.interaction_lists(cells, cells)
+        off, src = _lists(cells)
         K = oracle_ops(ell, kind, level)
         _ORACLE[key] = (oracle.m2l_apply_adjoint(K, cells, cells, off, src, w, len(cells)) if adjoint
                         else oracle.m2l_apply(K, cells, cells, off, src, w))
@@ -60,7 +69,7 @@ def _plan_apply(m2l, plan, w, prec, n_out, out_fp64=False, init=None):
 
 
 @pytest.mark.parametrize("prec", TC)
-@pytest.mark.parametrize("ell,kind,level,keep", [(4, 0, 4, 1.0), (5, 1, 4, 0.93), (3, 2, 4, 1.0), (2, 0, 5, 0.9)])
+@pytest.mark.parametrize("ell,kind,level,keep", [(2, 0, 5, 1.0), (3, 2, 5, 0.93), (4, 1, 5, 0.9)])
 def test_dense_matches_oracle(m2l, prec, ell, kind, level, keep):
     from paper_1210_7292_gb300 import synth
     cells = synth.full_grid(level) if keep == 1.0 else pruned_cells(level, keep, seed=ell * 11 + level)
@@ -83,7 +92,7 @@ def test_dense_fp64_locals_adjoint_and_bucketed_agree(m2l, prec):
     """One plan applied by both tensor-core kernels (the bucketed one through
     the M2L_DEBUG_NO_DENSE switch), FP64 locals, and the adjoint plan."""
     from paper_1210_7292_gb300 import synth
-    ell, level = 5, 4
+    ell, level = 4, 5
     cells = synth.full_grid(level)
     w = synth.gaussian_vectors(len(cells), ell ** 3, seed=301)
     lv = make_level(m2l, cells, level)
@@ -126,11 +135,34 @@ def test_dense_level5_sampled_and_repeatable(m2l):
     print("dense level 5 bf16x3 (%d units of %d): rel L2 %.2e" % (info["units"], info["unit_width"], err))
 
 
-def test_sparse_levels_keep_the_bucketed_kernel(m2l):
-    cells = pruned_cells(4, 0.4, 304)
-    lv = make_level(m2l, cells, 4)
-    plan = m2l.m2l_plan_create(gpu_ops(m2l, 4, 0, 4), lv)
-    assert not m2l.m2l_plan_kernel_info(plan)["dense"]
+def test_dense_level6_sampled(m2l):
+    """A full level 6 (262,144 cells, the differentiation workload's level),
+    ell = 3, 1/r^4, TF32x3 and BF16x3, sampled targets against the oracle."""
+    from paper_1210_7292_gb300 import synth
+    ell, level = 3, 6
+    cells = synth.full_grid(level)
+    w = synth.gaussian_vectors(len(cells), ell ** 3, seed=306)
+    lv = make_level(m2l, cells, level)
+    ops = gpu_ops(m2l, ell, 1, level)
+    plan = m2l.m2l_plan_create(ops, lv)
+    info = m2l.m2l_plan_kernel_info(plan)
+    assert info["dense"]
+    rng = np.random.default_rng(307)
+    samp = np.unique(np.concatenate([[0, len(cells) - 1], rng.choice(len(cells), 94, replace=False)]))
+    off, src = oracle.interaction_lists(cells[samp], cells)
+    ref = oracle.m2l_apply(oracle_ops(ell, 1, level), cells[samp], cells, off, src, w)
+    for prec in ("tf32x3", "bf16x3"):
+        got = _plan_apply(m2l, plan, w, prec, len(cells))
+        err = _check(got[samp], ref, prec)
+        print("dense level 6 %s (%d units of %d): rel L2 %.2e" % (prec, info["units"], info["unit_width"], err))
+
+
+def test_sparse_and_small_levels_keep_the_bucketed_kernel(m2l):
+    from paper_1210_7292_gb300 import synth
+    for cells, level in ((pruned_cells(5, 0.4, 304), 5), (synth.full_grid(4), 4)):
+        lv = make_level(m2l, cells, level)
+        plan = m2l.m2l_plan_create(gpu_ops(m2l, 4, 0, level), lv)
+        assert not m2l.m2l_plan_kernel_info(plan)["dense"], (level, len(cells))
 
 
 def test_dense_bounded_wait_reports_timeout(m2l):
@@ -138,7 +170,7 @@ def test_dense_bounded_wait_reports_timeout(m2l):
     stage, the MMA warp's bounded wait runs out, the kernel returns, the host
     reads M2L_ETIMEOUT and a correct apply follows on the same context."""
     from paper_1210_7292_gb300 import synth
-    ell, level = 4, 4
+    ell, level = 2, 5
     cells = synth.full_grid(level)
     w = synth.gaussian_vectors(len(cells), ell ** 3, seed=305)
     lv = make_level(m2l, cells, level)
