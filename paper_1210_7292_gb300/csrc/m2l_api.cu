@@ -119,6 +119,10 @@ static m2l_status dispatch(const m2l_ops *ops, const Buckets &b, const void *in,
 {
     if (b.nnz > 0 && (!in || !out)) { set_error("null vector pointer"); return M2L_EINVAL; }
     if (m2l_status st = check_device(ops)) return st;
+    const bool tc = precision == M2L_TF32 || precision == M2L_BF16X3 || precision == M2L_TF32X3;
+    const bool dense = tc && b.dense.valid && !(ops->debug_flags & M2L_DEBUG_NO_DENSE);
+    if (b.nnz > 0 && !dense)
+        if (m2l_status st = ensure_records(ops, b, s)) return st;
     switch (precision) {
     case M2L_FP64:
     case M2L_FP32:
@@ -411,6 +415,8 @@ m2l_status m2l_ops_prepare(const m2l_ops *ops, int precision, void *stream)
 m2l_status m2l_plan_query(const m2l_plan *plan, int64_t *counts16, int32_t *records, int64_t *nvalid)
 {
     if (!plan) { set_error("null plan"); return M2L_EINVAL; }
+    M2L_CUDA(cudaDeviceSynchronize());
+    if (m2l_status st = ensure_records(plan->ops, plan->b, 0)) return st;
     M2L_CUDA(cudaDeviceSynchronize());
     int32_t off[18] = {0};
     if (plan->b.nnz > 0) M2L_CUDA(cudaMemcpy(off, plan->b.class_off.p, sizeof(off), cudaMemcpyDeviceToHost));

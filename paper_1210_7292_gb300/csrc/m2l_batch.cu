@@ -84,6 +84,7 @@ extern "C" m2l_status m2l_batch_create(const m2l_plan *const *plans, int nbatch,
         if (m2l_status st = check_device(ops)) return st;
         if (ops->eps > 0) { set_error("the persistent batch takes full-rank operators"); return M2L_EUNSUPPORTED; }
         m2l_status st = prepare_simt_layout(ops, fp64, s);
+        if (st == M2L_OK && pl->b.nnz > 0) st = ensure_records(ops, pl->b, s);
         if (st != M2L_OK) return st;
         int32_t off[18] = {0};
         if (pl->b.nnz > 0) {

@@ -305,8 +305,20 @@ static m2l_status bucket(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const 
 {
     m2l_status st;
     b.dense.valid = false;
+    b.have_rec = true;
     const int nseg = (nnz + kSegEntries - 1) / kSegEntries;
     if ((st = b.rec.ensure((size_t)(nnz > 0 ? nnz : 1) * sizeof(int2))) != M2L_OK) return st;
+    if (nnz > 0 && dense_eligible(ops, ntgt, nnz)) {
+        // full level: the dense classification only; the operator buckets are derived
+        // from it if a bucketed kernel is asked for (their buffers are allocated now)
+        if ((st = b.class_off.ensure(18 * sizeof(int32_t))) != M2L_OK) return st;
+        b.nnz = nnz;
+        b.ntgt = ntgt;
+        b.nsrc = nsrc;
+        st = dense_classify(ops, ntgt, nsrc, nnz, tgt_ijk, src_ijk, offsets, sources, b.dense, s);
+        if (st == M2L_OK) b.have_rec = false;
+        return st;
+    }
     if ((st = b.tgt_of.ensure((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t))) != M2L_OK) return st;
     if ((st = b.code.ensure((size_t)(nnz > 0 ? nnz : 1) * sizeof(uint16_t))) != M2L_OK) return st;
     if ((st = b.seg.ensure((size_t)(17 * (size_t)nseg + 1) * 2 * sizeof(int32_t))) != M2L_OK) return st;
@@ -338,9 +350,6 @@ static m2l_status bucket(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const 
     scatter_kernel<<<nseg, kSegWarps * 32, 0, s>>>(nnz, nseg, b.code.as<uint16_t>(), b.tgt_of.as<int32_t>(), sources,
                                                     pos, b.class_off.as<int32_t>(), b.rec.as<int2>());
     M2L_LAUNCH_CHECK("scatter_kernel");
-    // full levels are also classified for the target-stationary tensor-core kernel
-    if (dense_eligible(ops, ntgt, nnz))
-        return dense_classify(ops, ntgt, nsrc, nnz, tgt_ijk, src_ijk, offsets, sources, b.dense, s);
     return M2L_OK;
 }
 

@@ -741,3 +741,120 @@ m2l_status launch_tc_dense(const m2l_ops *ops, const DenseBuckets &d, int precis
 }
 
 }  // namespace m2l
+
+// ---------------------------------------------------------------- operator buckets from the dense tables
+// For the kernels that take operator buckets (the CUDA-core precisions, the
+// bucketed tensor-core kernel), the records are derived from a dense
+// classification on demand: one warp per 32 columns of a unit, lane = column,
+// walking the unit's active slots (the operator class p of a slot is the same
+// for every lane).  Records of class p are ordered by (unit, column, slot), so
+// the entries of one target stay consecutive within a bucket.
+namespace m2l {
+namespace {
+
+constexpr int kRecWarps = 8;
+
+template <bool EMIT>
+__global__ void __launch_bounds__(kRecWarps * 32)
+dense_records_kernel(int umax, int nu, int nwarps, const int32_t *__restrict__ meta,
+                     const uint16_t *__restrict__ slots, const int32_t *__restrict__ tab,
+                     const int32_t *__restrict__ unit_tgt, const uint16_t *__restrict__ lut,
+                     int32_t *__restrict__ wcount, const int32_t *__restrict__ wbase, int2 *__restrict__ rec)
+{
+    __shared__ int cnt[kRecWarps][16][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kRecWarps + w;
+    const int per_unit = (nu + 31) / 32;
+    const int u = gw / per_unit;
+    const int j = (gw - u * per_unit) * 32 + lane;
+    const bool live = gw < nwarps && u < meta[0];
+    const bool col = live && j < nu;
+    for (int p = 0; p < 16; ++p) cnt[w][p][lane] = 0;
+    __syncwarp();
+    const uint16_t *row = slots + (size_t)(live ? u : 0) * kSlotRow;
+    const int ns = live ? row[0] : 0;
+    const int32_t *tcol = tab + (size_t)(live ? u : 0) * kSlots * nu + (col ? j : 0);
+    for (int si = 0; si < ns; ++si) {
+        const int slot = row[1 + si];
+        const int e = col ? tcol[(size_t)slot * nu] : 0;
+        if (e) ++cnt[w][lut[slot] & 0xFF][lane];
+    }
+    __syncwarp();
+    // exclusive prefix over the lanes, per class
+    int pre[16];
+#pragma unroll
+    for (int p = 0; p < 16; ++p) {
+        const int c = cnt[w][p][lane];
+        int incl = c;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += v;
+        }
+        pre[p] = incl - c;
+        if (!EMIT && lane == 31 && gw < nwarps) wcount[(size_t)p * nwarps + gw] = incl;
+    }
+    if (!EMIT) return;
+    const int tgt = col ? unit_tgt[(size_t)u * nu + j] : -1;
+    if (col) {
+#pragma unroll
+        for (int p = 0; p < 16; ++p) cnt[w][p][lane] = wbase[(size_t)p * nwarps + gw] + pre[p];
+    }
+    __syncwarp();
+    for (int si = 0; si < ns; ++si) {
+        const int slot = row[1 + si];
+        const int e = col ? tcol[(size_t)slot * nu] : 0;
+        if (e) {
+            const int c = lut[slot];
+            const int p = c & 0xFF, g = c >> 8;
+            rec[cnt[w][p][lane]++] = make_int2(e - 1, rec_pack(tgt, g));
+        }
+    }
+}
+
+__global__ void dense_class_off_kernel(int nwarps, int nnz, const int32_t *__restrict__ wbase, int32_t *__restrict__ class_off)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int p = 0; p < 16; ++p) class_off[p] = wbase[(size_t)p * nwarps];
+    class_off[16] = wbase[(size_t)16 * nwarps];
+    class_off[17] = nnz;
+}
+
+}  // namespace
+
+m2l_status ensure_records(const m2l_ops *ops, const Buckets &bc, cudaStream_t s)
+{
+    Buckets &b = const_cast<Buckets &>(bc);
+    if (b.have_rec) return M2L_OK;
+    const DenseBuckets &d = b.dense;
+    if (!d.valid) {
+        set_error("no classification to derive operator buckets from");
+        return M2L_EINVAL;
+    }
+    const int per_unit = (d.nu + 31) / 32;
+    const int nwarps = d.umax * per_unit;
+    const int nblk = (d.ntgt + kRankBlock - 1) / kRankBlock;
+    // the slot-flag region of the classification scratch holds the counts and their scan
+    int32_t *wcount = d.work.as<int32_t>() + 2 * (size_t)d.ntgt + 2 * (8 * (size_t)nblk + 1);
+    int32_t *wbase = wcount + 16 * (size_t)nwarps + 1;
+    if ((size_t)(2 * (16 * (size_t)nwarps + 1)) > (size_t)d.umax * kSlots) {
+        set_error("record scratch exceeds the classification scratch");
+        return M2L_EINVAL;
+    }
+    const int blocks = (nwarps + kRecWarps - 1) / kRecWarps;
+    dense_records_kernel<false><<<blocks, kRecWarps * 32, 0, s>>>(
+        d.umax, d.nu, nwarps, d.meta.as<int32_t>(), d.slots.as<uint16_t>(), d.tab.as<int32_t>(),
+        d.unit_tgt.as<int32_t>(), ops->lut.as<uint16_t>(), wcount, nullptr, nullptr);
+    M2L_LAUNCH_CHECK("dense_records_kernel");
+    m2l_status st = launch_exclusive_scan(wcount, wbase, 16 * nwarps, s);
+    if (st != M2L_OK) return st;
+    dense_class_off_kernel<<<1, 32, 0, s>>>(nwarps, d.nnz, wbase, b.class_off.as<int32_t>());
+    M2L_LAUNCH_CHECK("dense_class_off_kernel");
+    dense_records_kernel<true><<<blocks, kRecWarps * 32, 0, s>>>(
+        d.umax, d.nu, nwarps, d.meta.as<int32_t>(), d.slots.as<uint16_t>(), d.tab.as<int32_t>(),
+        d.unit_tgt.as<int32_t>(), ops->lut.as<uint16_t>(), nullptr, wbase, b.rec.as<int2>());
+    M2L_LAUNCH_CHECK("dense_records_kernel");
+    b.have_rec = true;
+    return M2L_OK;
+}
+
+}  // namespace m2l

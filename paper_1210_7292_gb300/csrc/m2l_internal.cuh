@@ -117,7 +117,8 @@ struct Buckets {
     DevBuf class_off;  // int32 [18]: start of bucket p at [p], [16] = valid total, [17] = nnz
     // adjoint: transposed list (scratch)
     DevBuf t_off, t_src, t_cursor;
-    DenseBuckets dense;   // also filled for full levels that the dense kernel serves
+    DenseBuckets dense;   // filled instead of the buckets for full levels that the dense kernel serves
+    mutable bool have_rec = true;   // rec/class_off hold the buckets (else derived from dense on demand)
     int nnz = 0;
     int ntgt = 0;
     int nsrc = 0;
@@ -200,6 +201,9 @@ m2l_status dense_classify(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const
 m2l_status dense_prepare(const m2l_ops *ops, int precision, cudaStream_t s);
 m2l_status launch_tc_dense(const m2l_ops *ops, const DenseBuckets &d, int precision, const float *in, void *out,
                            int out_fp64, double scale, cudaStream_t s);
+// Fill b.rec / b.class_off from the dense classification if they are not built
+// (stream-ordered, no allocation).
+m2l_status ensure_records(const m2l_ops *ops, const Buckets &b, cudaStream_t s);
 
 // General tensor-core apply (the large-order kernel over ncls operator images
 // of vector length N <= 256; used by the directional M2L).  tc_general_config

@@ -188,3 +188,36 @@ def test_dense_bounded_wait_reports_timeout(m2l):
     off, src = oracle.interaction_lists(cells, cells)
     ref = oracle.m2l_apply(oracle_ops(ell, 0, level), cells, cells, off, src, w)
     _check(_plan_apply(m2l, plan, w, "bf16x3", len(cells)), ref, "bf16x3")
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_buckets_derived_from_dense_classification(m2l, adjoint):
+    """A full level is classified for the dense kernel only; asking for its
+    operator buckets derives them on the device.  As a set, the derived records
+    (source, target, g) are the oracle's classification of the level's list
+    (the transposed list for the adjoint), and the per-operator counts match."""
+    from paper_1210_7292_gb300 import synth
+    level = 5
+    cells = synth.full_grid(level)
+    lv = make_level(m2l, cells, level)
+    plan = m2l.m2l_plan_create(gpu_ops(m2l, 3, 0, level), lv, adjoint=adjoint)
+    assert m2l.m2l_plan_kernel_info(plan)["dense"]
+    counts, recs = m2l.m2l_plan_query(plan)
+    off, src = _lists(cells)
+    tgt = np.repeat(np.arange(len(cells)), np.diff(off))
+    if adjoint:
+        tgt, src = src.astype(np.int64), tgt
+    t = cells[tgt].astype(np.int64) - cells[src].astype(np.int64)
+    code = oracle.lut343()[(t[:, 0] + 3) + 7 * (t[:, 1] + 3) + 49 * (t[:, 2] + 3)].astype(np.int64)
+    assert np.array_equal(counts, np.bincount(code & 0xFF, minlength=16))
+    exp = np.stack([src, tgt, code >> 8], axis=1).astype(np.int64)
+    got = recs.astype(np.int64)
+    key = lambda a: np.lexsort((a[:, 2], a[:, 1], a[:, 0]))
+    assert np.array_equal(got[key(got)], exp[key(exp)])
+    # records of one operator are grouped, and within it each target's entries are consecutive
+    p_of = np.repeat(np.arange(16), counts)
+    assert np.array_equal(p_of, code[np.lexsort((code & 0xFF,))] & 0xFF)
+    for p in range(16):
+        tg = got[p_of == p, 1]
+        starts = np.flatnonzero(np.diff(tg) != 0).size + 1
+        assert starts == np.unique(tg).size, p
