@@ -736,6 +736,81 @@ def fmm_matvec(m2l, device, precision, reps=5):
             "note": "P2M, M2M, M2L (levels 2-5), L2L, L2P and near field, particles resident on the GPU"}
 
 
+def config5_differentiation(m2l, device, mm, peaks, reps=3):
+    """The differentiation workload: full level 6 (262,144 cells), ell = 5,
+    1/r, loss = sum(W * M2L(w)) with w, W ~ N(0, 1) (seeds 5, 6); one step =
+    forward M2L + backward (the adjoint M2L) through torch.autograd, with plans
+    classified once.  Per precision: step time, interactions/s counting both
+    directions, algorithmic GFLOP/s (2 ell^6 per interaction and direction),
+    the roofline fraction of the apply kernels, and the gradient's rel. L2
+    against the FP64 gradient."""
+    import torch
+
+    from paper_1210_7292_gb300 import autograd, synth
+    level, ell = 6, ELL
+    n3 = ell ** 3
+    cells = synth.full_grid(level)
+    ijk = torch.from_numpy(cells).to(device)
+    off, src = m2l.m2l_build_lists(ijk, ijk)
+    lv = m2l.Level(2.0 / (1 << level), ijk, ijk, off, src, level)
+    nnz = lv.nnz
+    ops = m2l.m2l_precompute(m2l.M2L_K_INV_R, ell)
+    w64 = torch.from_numpy(synth.gaussian_vectors(len(cells), n3, seed=5)).to(device)
+    W64 = torch.from_numpy(synth.gaussian_vectors(len(cells), n3, seed=6)).to(device)
+    flops = 2.0 * n3 * n3 * nnz * 2
+    bf = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])
+    peak = {"fp64": mm["fp64"], "fp32": mm["fp32"], "tf32x3": mm["tf32"] / 3.0, "bf16x3": bf / 3.0}
+    out = {"workload": "full level 6 (262,144 cells), ell 5, 1/r, loss = sum(W * M2L(w)), w, W ~ N(0,1) seeds 5, 6",
+           "interactions_per_direction": nnz, "flop_convention": "2 ell^6 per interaction and direction"}
+    grads = {}
+    for prec in ("fp64", "fp32", "tf32x3", "bf16x3"):
+        op = autograd.M2LLevelOperator(ops, lv, prec)
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        w, W = w64.to(dt), W64.to(dt)
+
+        def step():
+            x = w.clone().requires_grad_(True)
+            loss = (W * op(x)).sum()
+            loss.backward()
+            return x.grad
+
+        g = step()
+        torch.cuda.synchronize(device)
+        grads[prec] = g.double()
+        n = 1 if prec == "fp64" else reps
+        ts, tf, tb = [], [], []
+        for _ in range(n):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record()
+            step()
+            e[1].record()
+            op.apply_forward(w)
+            e[2].record()
+            op.apply_adjoint(W)
+            e[3].record()
+            torch.cuda.synchronize(device)
+            ts.append(e[0].elapsed_time(e[1]))
+            tf.append(e[1].elapsed_time(e[2]))
+            tb.append(e[2].elapsed_time(e[3]))
+        ms = statistics.median(ts)
+        res = {"step_ms": ms, "forward_ms": statistics.median(tf), "adjoint_ms": statistics.median(tb),
+               "interactions_per_s": 2 * nnz / (ms / 1e3), "gflops": flops / (ms / 1e3) / 1e9,
+               "dense_kernel": m2l.m2l_plan_kernel_info(op.fwd)["dense"] and prec not in ("fp64", "fp32")}
+        kern_ms = res["forward_ms"] + res["adjoint_ms"]
+        res["roofline"] = {"achieved_tflops": flops / (kern_ms / 1e3) / 1e12, "peak_tflops": peak[prec],
+                           "frac": flops / (kern_ms / 1e3) / 1e12 / peak[prec],
+                           "peak_source": {"fp64": "FP64 matmul, this run", "fp32": "FP32 matmul, this run",
+                                           "tf32x3": "TF32 matmul, this run / 3",
+                                           "bf16x3": "bf16 burst (MEASURED_PEAKS.json) / 3"}[prec]}
+        out[prec] = res
+        m2l.m2l_sync_status(ops)
+        del op
+    ref = grads["fp64"]
+    for prec in ("fp32", "tf32x3", "bf16x3"):
+        out[prec]["grad_rel_l2_vs_fp64"] = float(torch.linalg.norm(grads[prec] - ref) / torch.linalg.norm(ref))
+    return out
+
+
 def direct_sum_at(pts, q, samp, device, chunk=16):
     """f_i = sum_{j != i} q_j / |x_i - x_j| at the sampled particles (Eq. (1)),
     in FP64 with torch on the GPU: the exact reference of the error figure
@@ -865,6 +940,7 @@ def run_ours(args):
     variants = variants_compare(m2l, device, wl, flush) if (rank == 0 and not args.quick) else None
     dfmm = dfmm_m2l(m2l, device, mm) if (rank == 0 and not args.quick) else None
     cfg3 = config3_levels(m2l, device) if (rank == 0 and not args.quick) else None
+    cfg5 = config5_differentiation(m2l, device, mm, peaks) if (rank == 0 and not args.quick) else None
     eqerr = (fmm_equal_error(m2l, device, ["fp64", "fp32", "tf32x3", "bf16x3", "tf32"])
              if (rank == 0 and not args.quick) else None)
     cpu = None
@@ -900,6 +976,7 @@ def run_ours(args):
                 "variants": variants,
                 "dfmm_m2l": dfmm,
                 "config3": cfg3,
+                "config5": cfg5,
                 "clocks": clk,
                 "precisions": extra}
         print(json.dumps(line), flush=True)
