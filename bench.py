@@ -424,11 +424,12 @@ def traffic_for(kernel_name):
     return ent["dram_bytes_per_launch"] if h == ent.get("source_sha256_16") else None
 
 
+# the level-5 launch: full levels take the target-stationary tensor-core kernel
 KERNEL_FOR = {"fp64": ("simt_apply_kernel<double>", "m2l_apply_simt.cu", "alu"),
               "fp32": ("simt_apply_kernel<float>", "m2l_apply_simt.cu", "alu"),
-              "tf32": ("tc_apply_kernel<tf32>", "m2l_apply_tc.cu", "tensor"),
-              "bf16x3": ("tc_apply_kernel<bf16x3>", "m2l_apply_tc.cu", "tensor"),
-              "tf32x3": ("tc_apply_kernel<tf32x3>", "m2l_apply_tc.cu", "tensor")}
+              "tf32": ("tc_dense_kernel<tf32>", "m2l_dense.cu", "tensor"),
+              "bf16x3": ("tc_dense_kernel<bf16x3>", "m2l_dense.cu", "tensor"),
+              "tf32x3": ("tc_dense_kernel<tf32x3>", "m2l_dense.cu", "tensor")}
 
 
 def matmul_peaks(device, n=8192):
