@@ -247,27 +247,40 @@ m2l_status m2l_plan_classify(m2l_plan *plan, const m2l_level *level, void *strea
  * precision), M2L_EUNSUPPORTED (as the apply would return). */
 m2l_status m2l_ops_prepare(const m2l_ops *ops, int precision, void *stream);
 
-/* Batched apply: nbatch independent (ops, level) problems.  For M2L_FP32 and
- * M2L_FP64 the problems are classified (one plan each) and then applied by ONE
- * persistent launch (m2l_batch_create/run/free inside the call; the call
- * synchronises `stream` and allocates its plans -- create an m2l_batch once for
- * repeated or graph-captured use).  Tensor-core precisions apply the problems
- * one launch each.  in[i], out[i] follow the types of m2l_apply_level. */
+/* Batched apply: nbatch independent (ops, level) problems, classified (one
+ * plan each) and then applied as an m2l_batch (m2l_batch_create/run/free
+ * inside the call; the call synchronises `stream` and allocates its plans --
+ * create an m2l_batch once for repeated or graph-captured use).  Tensor-core
+ * precisions with FP64 locals, orders above 6 or low-rank operators apply the
+ * problems one launch each.  in[i], out[i] follow the types of m2l_apply_level. */
 m2l_status m2l_apply_batch(const m2l_ops *const *ops, const m2l_level *levels,
                            const void *const *multipoles, void *const *locals, int nbatch,
                            int precision, int locals_fp64, void *stream);
 
 /* Persistent batches (the batched-trees workload): a fixed set of planned
- * translations -- any mix of trees, levels and orders ell <= 7 -- run by ONE
- * persistent kernel launch over a global tile queue.  precision: M2L_FP32 or
- * M2L_FP64 (CUDA-core products; out_fp64 selects double outputs for FP32).
+ * translations -- any mix of trees, levels, orders and operator sets -- run
+ * by persistent kernel launches over a global tile queue (the blocking of
+ * Alg. 2 along many target cells, Sec. 4.2.3, extended across problems).
+ *  - M2L_FP32, M2L_FP64: CUDA-core products, ONE launch over every problem
+ *    (ell <= 7; out_fp64 selects double outputs for FP32);
+ *  - M2L_TF32, M2L_BF16X3, M2L_TF32X3: tcgen05 products, ONE launch per
+ *    vector length ell^3 over every problem of that order (ell <= 6), each
+ *    class (problem, unique operator) with its operator image -- images built
+ *    once per distinct operator set and scale; per order the problems' input
+ *    vectors are gathered into one array by a kernel and the results added
+ *    back by another (FP32 outputs only).
  * in[i], out[i]: device vectors of plan i (types as m2l_plan_apply).
  * Creation reads the plans' bucket sizes (synchronises `stream`), picks the
- * tile width with a built-in autotuner (each candidate timed on scratch
- * outputs; the choice is cached per precision, padded order and interaction
- * count), and uploads the descriptor table.  m2l_batch_run allocates nothing
- * and issues one kernel launch, so it may be captured in a CUDA graph; the
- * plans and vectors must outlive the batch.  Full-rank operators only. */
+ * tile shape with a built-in autotuner -- each candidate timed on scratch
+ * outputs: tile width 32 or 64 for the CUDA cores; for the tensor cores, tile
+ * width 32 or 64 interactions and one or two epilogue groups wherever they fit
+ * shared memory -- cached per precision, order and interaction count, and
+ * uploads the descriptor tables.  m2l_batch_run allocates nothing and issues a
+ * fixed sequence of launches, so it may be captured in a CUDA graph; the
+ * plans and vectors must outlive the batch, and the batch copies the plans'
+ * buckets at creation (re-classifying a plan does not change the batch).
+ * List errors found on the device are reported to the status word of the
+ * first plan's operators.  Full-rank operators only. */
 typedef struct m2l_batch m2l_batch;
 m2l_status m2l_batch_create(const m2l_plan *const *plans, int nbatch, const void *const *in, void *const *out,
                             int precision, int out_fp64, void *stream, m2l_batch **out_batch);
@@ -275,6 +288,13 @@ m2l_status m2l_batch_run(const m2l_batch *batch, void *stream);
 /* tile_width: columns per tile chosen by the autotuner; tiles: tiles per run;
  * tuned_ms: the autotuner's best time (0 when taken from its cache). */
 m2l_status m2l_batch_info(const m2l_batch *batch, int *tile_width, int64_t *tiles, double *tuned_ms);
+/* Per launch group of a batch (host-side): ell3[i] the vector length of group
+ * i (the padded order of the CUDA-core batch's single group), tile_width[i]
+ * and epilogue_groups[i] the autotuner's choice (0 epilogue groups for the
+ * CUDA cores); up to max_groups entries are written, *ngroups receives the
+ * number of groups. */
+m2l_status m2l_batch_groups(const m2l_batch *batch, int max_groups, int32_t *ell3, int32_t *tile_width,
+                            int32_t *epilogue_groups, int32_t *ngroups);
 void m2l_batch_free(m2l_batch *batch);
 
 /* ---------------------------------------------------------------------

@@ -466,7 +466,12 @@ m2l_status m2l_apply_batch(const m2l_ops *const *ops, const m2l_level *levels, c
         set_error("bad batch arguments");
         return M2L_EINVAL;
     }
-    if (precision != M2L_FP32 && precision != M2L_FP64) {
+    bool loop = precision != M2L_FP32 && precision != M2L_FP64 && locals_fp64 != 0;
+    for (int i = 0; i < nbatch && !loop; ++i)
+        if (precision != M2L_FP32 && precision != M2L_FP64 && (!ops[i] || ops[i]->n3 > 256 || ops[i]->eps > 0))
+            loop = true;
+    if (loop) {
+        // FP64 outputs, orders above 6 or low-rank operators on the tensor cores: one apply per problem
         for (int i = 0; i < nbatch; ++i) {
             m2l_status st = m2l_apply_level(ops[i], &levels[i], multipoles[i], locals[i], precision, locals_fp64, stream);
             if (st != M2L_OK) return st;

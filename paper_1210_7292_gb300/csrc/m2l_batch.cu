@@ -55,6 +55,7 @@ struct m2l_batch {
     double tuned_ms = 0.0;
     long long nnz = 0;
     m2l::DevBuf descs;
+    m2l::TcBatch *tc = nullptr;   // tensor-core precisions
 };
 
 using namespace m2l;
@@ -68,9 +69,22 @@ extern "C" m2l_status m2l_batch_create(const m2l_plan *const *plans, int nbatch,
         return M2L_EINVAL;
     }
     *out_batch = nullptr;
+    if (precision == M2L_TF32 || precision == M2L_BF16X3 || precision == M2L_TF32X3) {
+        if (out_fp64) { set_error("the tensor-core batch writes FP32 outputs"); return M2L_EUNSUPPORTED; }
+        for (int i = 0; i < nbatch; ++i)
+            if (!plans[i] || !in[i] || !out[i]) { set_error("null plan or vector in batch entry %d", i); return M2L_EINVAL; }
+        TcBatch *tc = nullptr;
+        m2l_status st = tc_batch_create(plans, nbatch, in, out, precision, (cudaStream_t)stream, &tc);
+        if (st != M2L_OK) return st;
+        m2l_batch *b = new m2l_batch();
+        b->nprob = nbatch;
+        b->tc = tc;
+        *out_batch = b;
+        return M2L_OK;
+    }
     if (precision != M2L_FP32 && precision != M2L_FP64) {
-        set_error("the persistent batch runs M2L_FP32 or M2L_FP64 products");
-        return M2L_EUNSUPPORTED;
+        set_error("unknown precision %d", precision);
+        return M2L_EINVAL;
     }
     const int fp64 = precision == M2L_FP64;
     cudaStream_t s = (cudaStream_t)stream;
@@ -201,6 +215,7 @@ extern "C" m2l_status m2l_batch_create(const m2l_plan *const *plans, int nbatch,
 extern "C" m2l_status m2l_batch_run(const m2l_batch *b, void *stream)
 {
     if (!b) { set_error("null batch"); return M2L_EINVAL; }
+    if (b->tc) return tc_batch_run(b->tc, (cudaStream_t)stream);
     return launch_simt_batch(b->descs.as<BatchDesc>(), b->nprob, b->total_tiles, b->fp64, b->nt, b->kpad_max,
                              b->mpad_max, (cudaStream_t)stream);
 }
@@ -208,6 +223,10 @@ extern "C" m2l_status m2l_batch_run(const m2l_batch *b, void *stream)
 extern "C" m2l_status m2l_batch_info(const m2l_batch *b, int *tile_width, int64_t *tiles, double *tuned_ms)
 {
     if (!b) { set_error("null batch"); return M2L_EINVAL; }
+    if (b->tc) {
+        tc_batch_info(b->tc, tile_width, tiles, tuned_ms, nullptr, nullptr);
+        return M2L_OK;
+    }
     if (tile_width) *tile_width = b->nt;
     if (tiles) *tiles = b->total_tiles;
     if (tuned_ms) *tuned_ms = b->tuned_ms;
@@ -219,5 +238,34 @@ extern "C" void m2l_batch_free(m2l_batch *b)
     if (!b) return;
     cudaDeviceSynchronize();
     b->descs.release();
+    if (b->tc) tc_batch_free(b->tc);
     delete b;
+}
+
+extern "C" m2l_status m2l_batch_groups(const m2l_batch *b, int max_groups, int32_t *ell3, int32_t *tile_width,
+                                       int32_t *epilogue_groups, int32_t *ngroups)
+{
+    if (!b || max_groups < 0 || (max_groups > 0 && (!ell3 || !tile_width || !epilogue_groups))) {
+        set_error("bad batch or output arrays");
+        return M2L_EINVAL;
+    }
+    if (!b->tc) {
+        // the CUDA-core batch is one launch over every problem
+        if (max_groups > 0) {
+            ell3[0] = b->mpad_max;
+            tile_width[0] = b->nt;
+            epilogue_groups[0] = 0;
+        }
+        if (ngroups) *ngroups = 1;
+        return M2L_OK;
+    }
+    std::vector<int> n3(max_groups > 0 ? max_groups : 1), nt(n3.size()), eg(n3.size());
+    const int n = tc_batch_groups(b->tc, max_groups, n3.data(), nt.data(), eg.data());
+    for (int i = 0; i < n && i < max_groups; ++i) {
+        ell3[i] = n3[i];
+        tile_width[i] = nt[i];
+        epilogue_groups[i] = eg[i];
+    }
+    if (ngroups) *ngroups = n;
+    return M2L_OK;
 }

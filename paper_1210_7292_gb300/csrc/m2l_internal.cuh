@@ -216,6 +216,17 @@ m2l_status tc_general_apply(int precision, int N, int ncls, const int *tile_star
                             const int *class_off, const uint8_t *img, const int16_t *tinv, int nnz, const float *in,
                             float *out, int *status, cudaStream_t s);
 
+// Persistent batches on the tensor cores (m2l_batch_tc.cu): per vector length one
+// launch of the large-order kernel over all problems' (problem, operator) classes.
+struct TcBatch;
+m2l_status tc_batch_create(const m2l_plan *const *plans, int nbatch, const void *const *in, void *const *out,
+                           int precision, cudaStream_t s, TcBatch **out_batch);
+m2l_status tc_batch_run(const TcBatch *b, cudaStream_t s);
+void tc_batch_info(const TcBatch *b, int *tile_width, int64_t *tiles, double *tuned_ms, int *epilogue_groups,
+                   int *launches);
+int tc_batch_groups(const TcBatch *b, int max, int *n3, int *tile_width, int *epilogue_groups);
+void tc_batch_free(TcBatch *b);
+
 // One problem of a batched persistent launch (host-built, copied to the device).
 struct BatchDesc {
     const int2 *rec;          // bucketed records of the problem

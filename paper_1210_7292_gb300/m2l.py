@@ -85,6 +85,7 @@ def lib():
             "m2l_batch_create": [P, I, P, P, I, I, P, ctypes.POINTER(P)],
             "m2l_batch_run": [P, P],
             "m2l_batch_info": [P, P, P, P],
+            "m2l_batch_groups": [P, I, P, P, P, P],
             "m2l_sync_status": [P, P],
             "m2l_ops_set_debug": [P, I],
             "m2l_sa_create": [P, D, I, P, ctypes.POINTER(P)],
@@ -410,7 +411,8 @@ class Batch:
 
 
 def m2l_batch_create(plans, ins, outs, precision="fp32", out_fp64=False, stream=None) -> Batch:
-    """One persistent launch over a fixed set of planned translations (FP32/FP64)."""
+    """Persistent launches over a fixed set of planned translations: one for the
+    CUDA-core precisions, one per order for the tensor-core ones."""
     n = len(plans)
     p, tin, tout = _vec_dtypes(precision, out_fp64)
     for pl, a, b in zip(plans, ins, outs):
@@ -433,6 +435,17 @@ def m2l_batch_info(batch: Batch):
     _check("m2l_batch_info", lib().m2l_batch_info(batch.handle, ctypes.byref(nt), ctypes.byref(tiles),
                                                   ctypes.byref(ms)))
     return {"tile_width": nt.value, "tiles": tiles.value, "tuned_ms": ms.value}
+
+
+def m2l_batch_groups(batch: Batch):
+    """[(ell^3, tile width, epilogue groups)] of each launch group of the batch."""
+    n = ctypes.c_int32()
+    _check("m2l_batch_groups", lib().m2l_batch_groups(batch.handle, 0, None, None, None, ctypes.byref(n)))
+    k = max(n.value, 1)
+    e3, nt, eg = (np.zeros(k, dtype=np.int32) for _ in range(3))
+    _check("m2l_batch_groups", lib().m2l_batch_groups(batch.handle, k, e3.ctypes.data, nt.ctypes.data,
+                                                      eg.ctypes.data, ctypes.byref(n)))
+    return [(int(e3[i]), int(nt[i]), int(eg[i])) for i in range(n.value)]
 
 
 def m2l_build_lists(tgt_ijk, src_ijk, stream=None):

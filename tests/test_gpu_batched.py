@@ -1,7 +1,8 @@
 """The batched-trees workload: 64 independent octrees (N log-uniform in
 [1e4, 1e6], uniform cube and sphere surface alternating, leaf levels 3-6,
 ell in {4, 5, 6}), kernel 1/sqrt(r^2 + c^2) with c = 0.01, FP32; all levels of
-all trees in ONE persistent launch, captured in a CUDA graph and replayed.
+all trees in ONE persistent launch on the CUDA cores, or one per order on the
+tensor cores (TF32x3, BF16x3), captured in a CUDA graph and replayed.
 Checked against the oracle on sampled targets of every problem."""
 import numpy as np
 import pytest
@@ -110,6 +111,60 @@ def test_batched_trees_one_launch_and_graph(m2l):
           % (len(probs), nint, info["tile_width"], ms, nint / ms * 1e3))
 
 
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_batched_trees_tensor_cores(m2l, prec):
+    """The same 64 trees on the tcgen05 tensor cores: one persistent launch per
+    order (ell^3 = 64, 125, 216) over every tree and level of that order, tile
+    shapes from the autotuner, sampled targets against the oracle, and two
+    replays of a CUDA graph of the run giving twice the eager result."""
+    probs, _ = _problems(m2l, 64)
+    plans = [m2l.m2l_plan_create(p["ops"], p["lv"]) for p in probs]
+    ins = [torch.from_numpy(p["w"]).to(device(), torch.float32) for p in probs]
+    outs = [torch.zeros(p["lv"].struct.ncells_tgt, p["ell"] ** 3, dtype=torch.float32, device=device()) for p in probs]
+    batch = m2l.m2l_batch_create(plans, ins, outs, prec)
+    groups = m2l.m2l_batch_groups(batch)
+    assert sorted(g[0] for g in groups) == sorted({p["ell"] ** 3 for p in probs})
+    for _, nt, eg in groups:
+        assert nt in (32, 64) and eg in (1, 2)
+    before = m2l.m2l_launch_count()
+    m2l.m2l_batch_run(batch)
+    # per order: gather of the inputs, one persistent tensor-core launch, scatter of the outputs
+    assert m2l.m2l_launch_count() - before == 3 * len(groups)
+    torch.cuda.synchronize()
+    m2l.m2l_sync_status(probs[0]["ops"])
+    worst = _check_sampled(probs, outs, np.random.default_rng(7))
+    assert worst < TOL[prec], worst
+    eager = [o.clone() for o in outs]
+    for o in outs:
+        o.zero_()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            m2l.m2l_batch_run(batch, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    for o in outs:
+        o.zero_()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    m2l.m2l_sync_status(probs[0]["ops"])
+    for o, e in zip(outs, eager):
+        if float(e.abs().max()) > 0:
+            assert float((o - 2 * e).norm() / (2 * e).norm()) < 1e-5
+    nint = sum(p["lv"].nnz for p in probs)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(5):
+        g.replay()
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / 5
+    print("batched %s: %d problems, %d interactions, groups %s, graph replay %.3f ms, %.3e interactions/s"
+          % (prec, len(probs), nint, groups, ms, nint / ms * 1e3))
+
+
 def test_apply_batch_entry_point(m2l):
     probs, _ = _problems(m2l, 6)
     ins = [torch.from_numpy(p["w"]).to(device(), torch.float32) for p in probs]
@@ -123,3 +178,8 @@ def test_apply_batch_entry_point(m2l):
     m2l.m2l_apply_batch([p["ops"] for p in probs], [p["lv"] for p in probs], ins64, outs64, "fp64")
     worst = _check_sampled(probs, outs64, np.random.default_rng(6))
     assert worst < TOL["fp64"], worst
+    # a tensor-core precision through the same entry point (a batch per call)
+    outs_tc = [torch.zeros_like(o) for o in outs]
+    m2l.m2l_apply_batch([p["ops"] for p in probs], [p["lv"] for p in probs], ins, outs_tc, "tf32x3")
+    worst = _check_sampled(probs, outs_tc, np.random.default_rng(6))
+    assert worst < TOL["tf32x3"], worst
