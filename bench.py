@@ -737,6 +737,86 @@ def fmm_matvec(m2l, device, precision, reps=5):
             "note": "P2M, M2M, M2L (levels 2-5), L2L, L2P and near field, particles resident on the GPU"}
 
 
+def config4_batched(m2l, device, mm, peaks, reps=5):
+    """The batched workload: 64 independent trees (seed 4; N log-uniform in
+    [1e4, 1e6], uniform cube and sphere surface alternating, leaf levels 3-6,
+    ell in {4, 5, 6}), kernel 1/sqrt(r^2 + 0.01^2), every level 2..leaf of every
+    tree as one problem.  Per precision one m2l_batch (the autotuner picks its
+    tile shapes), its run captured in a CUDA graph and replayed: interactions/s,
+    algorithmic GFLOP/s (2 ell^6 per interaction), the roofline fraction, the
+    chosen shapes, and the rel. L2 of all outputs against the FP64 batch."""
+    import torch
+
+    from paper_1210_7292_gb300 import synth
+    c = 0.01
+    ops_cache, probs = {}, []
+    for spec in synth.batched_tree_specs(64, seed=4):
+        pts, _ = synth.tree_points(spec)
+        ell = spec["ell"]
+        for L in range(2, spec["leaf_level"] + 1):
+            cells = synth.occupied_cells(pts, L)
+            width = 2.0 / (1 << L)
+            if (ell, L) not in ops_cache:
+                ops_cache[(ell, L)] = m2l.m2l_precompute(m2l.M2L_K_INV_SQRT_R2C2, ell, 0.0, width, c)
+            ijk = torch.from_numpy(cells).to(device)
+            off, src = m2l.m2l_build_lists(ijk, ijk)
+            lv = m2l.Level(width, ijk, ijk, off, src, L)
+            w = synth.gaussian_vectors(len(cells), ell ** 3, seed=spec["seed"] * 10 + L)
+            probs.append((ops_cache[(ell, L)], lv, w, ell))
+    plans = [m2l.m2l_plan_create(o, lv) for o, lv, _, _ in probs]
+    nnz = sum(lv.nnz for _, lv, _, _ in probs)
+    flops = sum(2.0 * (ell ** 3) ** 2 * lv.nnz for _, lv, _, ell in probs)
+    bf = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])
+    peak = {"fp32": mm["fp32"], "tf32x3": mm["tf32"] / 3.0, "bf16x3": bf / 3.0}
+    out = {"workload": "64 trees (seed 4), N log-uniform 1e4-1e6, cube / sphere surface, leaf levels 3-6, "
+                       "ell 4-6, 1/sqrt(r^2 + 0.01^2), all levels 2..leaf",
+           "problems": len(probs), "interactions": nnz, "gflop": flops / 1e9}
+    res = {}
+    for prec in ("fp64", "fp32", "tf32x3", "bf16x3"):
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        ins = [torch.from_numpy(w).to(device, dt) for _, _, w, _ in probs]
+        outs = [torch.zeros(lv.struct.ncells_tgt, ell ** 3, dtype=dt, device=device) for _, lv, _, ell in probs]
+        t0 = time.perf_counter()
+        batch = m2l.m2l_batch_create(plans, ins, outs, prec)
+        create_ms = 1e3 * (time.perf_counter() - t0)
+        m2l.m2l_batch_run(batch)
+        torch.cuda.synchronize(device)
+        res[prec] = torch.cat([o.double().flatten() for o in outs])
+        s = torch.cuda.Stream(device=device)
+        s.wait_stream(torch.cuda.current_stream(device))
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                m2l.m2l_batch_run(batch, stream=s)
+        torch.cuda.current_stream(device).wait_stream(s)
+        g.replay()
+        torch.cuda.synchronize(device)
+        n = 1 if prec == "fp64" else reps
+        ts = []
+        for _ in range(n):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize(device)
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        info = m2l.m2l_batch_info(batch)
+        entry = {"graph_replay_ms": ms, "interactions_per_s": nnz / (ms / 1e3), "gflops": flops / (ms / 1e3) / 1e9,
+                 "create_ms_incl_autotune": round(create_ms, 1), "tiles": info["tiles"],
+                 "launch_groups": [{"ell3": e3, "tile_width": nt, "epilogue_groups": eg}
+                                   for e3, nt, eg in m2l.m2l_batch_groups(batch)]}
+        if prec in peak:
+            entry["roofline"] = {"achieved_tflops": flops / (ms / 1e3) / 1e12, "peak_tflops": peak[prec],
+                                 "frac": flops / (ms / 1e3) / 1e12 / peak[prec]}
+        out[prec] = entry
+        m2l.m2l_sync_status(probs[0][0])
+        del g, batch
+    for prec in ("fp32", "tf32x3", "bf16x3"):
+        out[prec]["rel_l2_vs_fp64"] = float(torch.linalg.norm(res[prec] - res["fp64"]) / torch.linalg.norm(res["fp64"]))
+    return out
+
+
 def config5_differentiation(m2l, device, mm, peaks, reps=3):
     """The differentiation workload: full level 6 (262,144 cells), ell = 5,
     1/r, loss = sum(W * M2L(w)) with w, W ~ N(0, 1) (seeds 5, 6); one step =
@@ -942,6 +1022,7 @@ def run_ours(args):
     dfmm = dfmm_m2l(m2l, device, mm) if (rank == 0 and not args.quick) else None
     cfg3 = config3_levels(m2l, device) if (rank == 0 and not args.quick) else None
     cfg5 = config5_differentiation(m2l, device, mm, peaks) if (rank == 0 and not args.quick) else None
+    cfg4 = config4_batched(m2l, device, mm, peaks) if (rank == 0 and not args.quick) else None
     eqerr = (fmm_equal_error(m2l, device, ["fp64", "fp32", "tf32x3", "bf16x3", "tf32"])
              if (rank == 0 and not args.quick) else None)
     cpu = None
@@ -977,6 +1058,7 @@ def run_ours(args):
                 "variants": variants,
                 "dfmm_m2l": dfmm,
                 "config3": cfg3,
+                "config4": cfg4,
                 "config5": cfg5,
                 "clocks": clk,
                 "precisions": extra}
