@@ -308,6 +308,7 @@ class Workload:
                             "off": off.cpu().pin_memory(), "src": src.cpu().pin_memory(),
                             "loc": torch.zeros(len(cells), ELL ** 3, dtype=self.dt_in).pin_memory()}
         self.total = sum(self.nint.values())
+        self.local_nint = dict(self.nint)
         assert self.nint[5] == full_interactions(5)
         # M2L at one level reads only that level's multipoles and lists and writes only its
         # locals, so the levels run concurrently: one stream and one plan (its own bucket
@@ -380,6 +381,119 @@ class Workload:
         for L in LEVELS:
             h = self.host[L]
             h2d += sum(t.numel() * t.element_size() for t in (h["mp"], h["ijk"], h["off"], h["src"]))
+            d2h += h["loc"].numel() * h["loc"].element_size()
+        return h2d, d2h
+
+
+class ShardedWorkload:
+    """The same hot path split by target ranges over the ranks (one process per
+    GPU): every level's target cells are cut into contiguous ranges; a rank
+    owns the multipoles and locals of its range and applies the level's lists
+    of its targets.  Per step and level: one all-gather of the level's
+    multipoles (the only exchange: sources lie within three cells of a target,
+    Sec. 3.2), then the rank's classification and apply on its shard."""
+
+    def __init__(self, m2l, device, precision, seed, rank, world):
+        import numpy as np
+        import torch
+
+        from paper_1210_7292_gb300 import shard, synth
+        self.m2l, self.device, self.precision, self.rank, self.world = m2l, device, precision, rank, world
+        self.shard = shard
+        self.ops = m2l.m2l_precompute(m2l.M2L_K_INV_R, ELL)
+        self.dt_in = torch.float64 if precision == "fp64" else torch.float32
+        self.levels, self.mine, self.loc, self.sh, self.ranges, self.nint = {}, {}, {}, {}, {}, {}
+        self.host = {}
+        for L in LEVELS:
+            cells = synth.full_grid(L)
+            ijk = torch.from_numpy(cells).to(device)
+            off, src = m2l.m2l_build_lists(ijk, ijk)
+            off, src = off.cpu().numpy(), src.cpu().numpy()
+            sh = shard.shard_level(off, src, rank, world)
+            t0, t1 = sh["t0"], sh["t1"]
+            tgt = torch.from_numpy(np.ascontiguousarray(cells[t0:t1])).to(device)
+            srcs = torch.from_numpy(np.ascontiguousarray(cells[sh["needed"]])).to(device)
+            self.levels[L] = m2l.Level(2.0 / (1 << L), tgt, srcs, torch.from_numpy(sh["offsets"]).to(device),
+                                       torch.from_numpy(sh["sources"]).to(device), L)
+            w = synth.gaussian_vectors(len(cells), ELL ** 3, seed=seed + 100 * L)
+            self.mine[L] = torch.from_numpy(np.ascontiguousarray(w[t0:t1])).to(device, self.dt_in)
+            self.loc[L] = torch.zeros(t1 - t0, ELL ** 3, dtype=self.dt_in, device=device)
+            self.sh[L] = sh
+            self.ranges[L] = shard.target_ranges(len(cells), world)
+            self.nint[L] = int(len(src))          # interactions of the whole level (all ranks)
+            self.host[L] = {"mine": self.mine[L].cpu().pin_memory(),
+                            "tgt": tgt.cpu().pin_memory(), "srcs": srcs.cpu().pin_memory(),
+                            "off": torch.from_numpy(sh["offsets"]).pin_memory(),
+                            "src": torch.from_numpy(sh["sources"]).pin_memory(),
+                            "loc": torch.zeros(t1 - t0, ELL ** 3, dtype=self.dt_in).pin_memory()}
+        self.total = sum(self.nint.values())
+        self.local_nint = {L: self.levels[L].nnz for L in LEVELS}
+        self.plans = {L: m2l.m2l_plan_create(self.ops, self.levels[L]) for L in LEVELS}
+        self.streams = {L: torch.cuda.Stream(device=device) for L in LEVELS}
+        torch.cuda.synchronize(device)
+
+    def step(self, kev=None):
+        import torch
+        m2l = self.m2l
+        cur = torch.cuda.current_stream(self.device)
+        m2l.m2l_ops_rebuild(self.ops, cur)
+        m2l.m2l_ops_prepare(self.ops, self.precision, cur)
+        ready = torch.cuda.Event()
+        ready.record(cur)
+        for L in sorted(LEVELS, reverse=True):
+            s = self.streams[L]
+            s.wait_event(ready)
+            with torch.cuda.stream(s):
+                halo = self.shard.exchange_multipoles(self.mine[L], self.ranges[L], self.sh[L]["needed"])
+                if kev is not None:
+                    kev[L][2].record(s)
+                m2l.m2l_plan_classify(self.plans[L], self.levels[L], s)
+                if kev is not None:
+                    kev[L][3].record(s)
+                    kev[L][0].record(s)
+                m2l.m2l_plan_apply(self.plans[L], halo, self.loc[L], self.precision, stream=s)
+                if kev is not None:
+                    kev[L][1].record(s)
+            done = torch.cuda.Event()
+            done.record(s)
+            cur.wait_event(done)
+
+    def e2e_step(self):
+        """The sharded step from pinned host buffers: the rank's multipoles and
+        shard lists in, the exchange, classification and apply, its locals out."""
+        import torch
+        m2l = self.m2l
+        cur = torch.cuda.current_stream(self.device)
+        m2l.m2l_ops_rebuild(self.ops, cur)
+        m2l.m2l_ops_prepare(self.ops, self.precision, cur)
+        ready = torch.cuda.Event()
+        ready.record(cur)
+        keep = {}
+        for L in sorted(LEVELS, reverse=True):
+            s = self.streams[L]
+            s.wait_event(ready)
+            h = self.host[L]
+            with torch.cuda.stream(s):
+                mine = h["mine"].to(self.device, non_blocking=True)
+                lv = m2l.Level(2.0 / (1 << L), h["tgt"].to(self.device, non_blocking=True),
+                               h["srcs"].to(self.device, non_blocking=True), h["off"].to(self.device, non_blocking=True),
+                               h["src"].to(self.device, non_blocking=True), L)
+                halo = self.shard.exchange_multipoles(mine, self.ranges[L], self.sh[L]["needed"])
+                loc = torch.zeros(lv.struct.ncells_tgt, ELL ** 3, dtype=self.dt_in, device=self.device)
+                m2l.m2l_plan_classify(self.plans[L], lv, s)
+                m2l.m2l_plan_apply(self.plans[L], halo, loc, self.precision, stream=s)
+                h["loc"].copy_(loc, non_blocking=True)
+            keep[L] = (lv, mine, halo, loc)
+            done = torch.cuda.Event()
+            done.record(s)
+            cur.wait_event(done)
+        return keep
+
+    def e2e_bytes(self):
+        h2d = d2h = 0
+        for L in LEVELS:
+            h = self.host[L]
+            h2d += sum(t.numel() * t.element_size() for t in (h["mine"], h["tgt"], h["srcs"], h["off"], h["src"]))
             d2h += h["loc"].numel() * h["loc"].element_size()
         return h2d, d2h
 
@@ -956,7 +1070,22 @@ def run_ours(args):
     g.build()
     from paper_1210_7292_gb300 import m2l
     prec = args.precision
-    wl = Workload(m2l, device, prec, SEED + rank)
+    sharded = world > 1 or args.shard
+    if sharded and world == 1:
+        # one rank of the sharded path (its single all-gather needs a process group)
+        import socket
+
+        import torch.distributed as dist
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        dist.init_process_group("nccl", init_method="tcp://127.0.0.1:%d" % port, rank=0, world_size=1)
+    if sharded:
+        wl = ShardedWorkload(m2l, device, prec, SEED, rank, world)
+        local5 = wl.levels[5].nnz
+    else:
+        wl = Workload(m2l, device, prec, SEED + rank)
+        local5 = wl.nint[5]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
     for _ in range(args.warmup):
         wl.step()
@@ -974,9 +1103,11 @@ def run_ours(args):
     barrier(world)
     m2l.m2l_sync_status(wl.ops)
     tmax = max_over_ranks(world, total, device)
-    value = world * wl.total * args.steps / tmax
+    # replicas: every rank runs the whole workload; shards: the ranks share one
+    units = wl.total if sharded else world * wl.total
+    value = units * args.steps / tmax
     k5 = statistics.mean(kt[5])
-    ach = FLOPS_PER_INTERACTION * wl.nint[5] / k5 / 1e12
+    ach = FLOPS_PER_INTERACTION * local5 / k5 / 1e12
     peaks, src_kind = measured_peaks()
     mm = matmul_peaks(device)
 
@@ -987,7 +1118,7 @@ def run_ours(args):
     barrier(world)
     e2e_total, _ = timed(wl.e2e_step, max(2, args.steps // 2), flush, device)
     e2e_max = max_over_ranks(world, e2e_total, device)
-    e2e_val = world * wl.total * max(2, args.steps // 2) / e2e_max
+    e2e_val = units * max(2, args.steps // 2) / e2e_max
     h2d, d2h = wl.e2e_bytes()
 
     # FP64 and the other precisions beside the headline, with their error vs FP64 at level 5
@@ -1018,7 +1149,8 @@ def run_ours(args):
                 extra[p] = {"unavailable": str(e)}
     fmm = fmm_matvec(m2l, device, prec) if (rank == 0 and not args.quick and prec != "fp64") else None
     pre = precompute_times(m2l, device) if (rank == 0 and not args.quick) else None
-    variants = variants_compare(m2l, device, wl, flush) if (rank == 0 and not args.quick) else None
+    wl_full = wl if not sharded else (Workload(m2l, device, prec, SEED) if (rank == 0 and not args.quick) else None)
+    variants = variants_compare(m2l, device, wl_full, flush) if (rank == 0 and not args.quick) else None
     dfmm = dfmm_m2l(m2l, device, mm) if (rank == 0 and not args.quick) else None
     cfg3 = config3_levels(m2l, device) if (rank == 0 and not args.quick) else None
     cfg5 = config5_differentiation(m2l, device, mm, peaks) if (rank == 0 and not args.quick) else None
@@ -1033,18 +1165,20 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64"}.get(prec, "f32"),
+                "scaling": "strong" if sharded else "weak", "vs_baseline": None,
+                "dtype": {"fp64": "f64"}.get(prec, "f32"),
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "precision": prec, "levels": list(LEVELS),
-                           "interactions_per_step_per_gpu": wl.total,
+                           "interactions_per_step_per_gpu": sum(wl.local_nint.values()),
                            "l2_policy": "inputs (49 MB) fit in L2: a 256 MB buffer is written between timed steps",
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                           "parallelism": ("target-range shards over %d rank(s), one multipole all-gather per level"
+                                           % world) if sharded else "single GPU"},
                 "gflops": value * FLOPS_PER_INTERACTION / 1e9,
                 "level5_kernel_ms": 1e3 * k5,
-                "per_level": {L: {"interactions": wl.nint[L], "apply_ms": 1e3 * statistics.mean(kt[L]),
+                "per_level": {L: {"interactions": wl.local_nint[L], "apply_ms": 1e3 * statistics.mean(kt[L]),
                                   "classify_ms": 1e3 * statistics.mean(kt["classify"][L]),
-                                  "interactions_per_s": wl.nint[L] / statistics.mean(kt[L]),
-                                  "gflops": FLOPS_PER_INTERACTION * wl.nint[L] / statistics.mean(kt[L]) / 1e9}
+                                  "interactions_per_s": wl.local_nint[L] / statistics.mean(kt[L]),
+                                  "gflops": FLOPS_PER_INTERACTION * wl.local_nint[L] / statistics.mean(kt[L]) / 1e9}
                               for L in LEVELS},
                 "roofline": roofline(prec, ach, peaks, src_kind, mm),
                 "matmul_peaks_tflops": mm,
@@ -1120,6 +1254,38 @@ def run_dfmm_apply_only(args):
     return 0
 
 
+def run_config3_apply_only(args):
+    """Level 6 of the mixed-precision workload (4M points on the ellipsoid, ell
+    = 7, 1/r^4), full-rank operators, three applies in --config3-precision:
+    for profiler captures of the large-order kernel."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_1210_7292_gb300 import m2l, synth
+    device = torch.device("cuda", 0)
+    pts, _ = synth.ellipsoid_surface(4_000_000, (1.0, 0.5, 0.25), seed=3)
+    L, ell = 6, 7
+    cells = synth.occupied_cells(pts, L)
+    ijk = torch.from_numpy(cells).to(device)
+    off, src = m2l.m2l_build_lists(ijk, ijk)
+    lv = m2l.Level(2.0 / (1 << L), ijk, ijk, off, src, L)
+    ops = m2l.m2l_precompute(m2l.M2L_K_INV_R4, ell)
+    plan = m2l.m2l_plan_create(ops, lv)
+    prec = args.config3_precision
+    w = torch.from_numpy(synth.gaussian_vectors(len(cells), ell ** 3, seed=33 + L)).to(device, torch.float32)
+    loc = torch.zeros(len(cells), ell ** 3, dtype=torch.float32, device=device)
+    m2l.m2l_ops_prepare(ops, prec)
+    for _ in range(3):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        m2l.m2l_plan_apply(plan, w, loc, prec)
+        e.record()
+        torch.cuda.synchronize()
+        log("config-3 level-6 apply (%s, %d interactions): %.3f ms" % (prec, lv.nnz, s.elapsed_time(e)))
+    m2l.m2l_sync_status(ops)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1131,10 +1297,16 @@ def main():
     ap.add_argument("--compare", default="fp32,tf32,tf32x3,bf16x3",
                     help="comma list of extra precisions to report (FP64 is always measured)")
     ap.add_argument("--quick", action="store_true", help="skip the extra precisions and the CPU baseline")
+    ap.add_argument("--shard", action="store_true",
+                    help="run the target-range sharded path even on one rank (it is the default for N > 1)")
     ap.add_argument("--apply-only", action="store_true",
                     help="run three level-5 apply launches only (for profiler captures)")
     ap.add_argument("--dfmm-apply-only", action="store_true",
                     help="run three directional level-5 apply launches only (for profiler captures)")
+    ap.add_argument("--config3-apply-only", action="store_true",
+                    help="run three level-6 applies of the mixed-precision workload only (for profiler captures)")
+    ap.add_argument("--config3-precision", default="bf16x3", choices=["fp32", "tf32", "bf16x3", "tf32x3"],
+                    help="precision of --config3-apply-only")
     ap.add_argument("--dfmm-precision", default="fp32", choices=["fp64", "fp32", "tf32", "bf16x3", "tf32x3"],
                     help="precision of --dfmm-apply-only")
     args = ap.parse_args()
@@ -1148,6 +1320,8 @@ def main():
         return run_apply_only(args)
     if args.dfmm_apply_only:
         return run_dfmm_apply_only(args)
+    if args.config3_apply_only:
+        return run_config3_apply_only(args)
     return run_ours(args)
 
 
