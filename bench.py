@@ -1197,8 +1197,8 @@ def run_ours(args):
                 "clocks": clk,
                 "precisions": extra}
         print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
         dist.destroy_process_group()
     return 0
 

@@ -299,11 +299,12 @@ void m2l_ops_free(m2l_ops *ops)
     ops->K64.release(); ops->sigma.release(); ops->lut.release(); ops->tsym.release();
     ops->U64.release(); ops->V64.release();
     Layout *ls[] = {&ops->simt64, &ops->simt32, &ops->lr64, &ops->lr32, &ops->tc_tf32, &ops->tc_bf16x3, &ops->tc_tf32x3,
-                    &ops->tcd_tf32, &ops->tcd_bf16x3, &ops->tcd_tf32x3};
+                    &ops->tcd_tf32, &ops->tcd_bf16x3, &ops->tcd_tf32x3, &ops->lrtc_tf32, &ops->lrtc_bf16x3,
+                    &ops->lrtc_tf32x3};
     for (Layout *l : ls) { l->a.release(); l->b.release(); }
     Buckets &b = ops->ws;
     b.rec.release(); b.tgt_of.release(); b.code.release(); b.seg.release(); b.class_off.release();
-    b.t_off.release(); b.t_src.release(); b.t_cursor.release(); b.dense.release();
+    b.t_off.release(); b.t_src.release(); b.t_cursor.release(); b.dense.release(); b.lrz.release();
     if (ops->d_status) cudaFree(ops->d_status);
     delete ops;
 }
@@ -455,7 +456,7 @@ void m2l_plan_free(m2l_plan *plan)
     cudaDeviceSynchronize();
     Buckets &b = plan->b;
     b.rec.release(); b.tgt_of.release(); b.code.release(); b.seg.release(); b.class_off.release();
-    b.t_off.release(); b.t_src.release(); b.t_cursor.release(); b.dense.release();
+    b.t_off.release(); b.t_src.release(); b.t_cursor.release(); b.dense.release(); b.lrz.release();
     delete plan;
 }
 

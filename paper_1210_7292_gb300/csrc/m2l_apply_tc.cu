@@ -550,16 +550,13 @@ m2l_status launch_kind(const m2l_ops *ops, const Buckets &b, Layout &L, const fl
                        double scale, cudaStream_t s)
 {
     using Tr = TcTraits<KIND>;
+    constexpr int prec = KIND == TC_TF32 ? M2L_TF32 : KIND == TC_BF16X3 ? M2L_BF16X3 : M2L_TF32X3;
     const int n3 = ops->n3;
-    if (ops->eps > 0) {
-        set_error("tensor-core precisions take full-rank operators");
-        return M2L_EUNSUPPORTED;
-    }
+    // per-operator low-rank factors: two passes of the large-order kernel
+    if (ops->eps > 0) return launch_tc_lowrank(ops, b, prec, in, out, out_fp64, scale, s);
     if (n3 > 128) return launch_big_ell<KIND>(ops, b, L, in, out, out_fp64, scale, s);
-    if (b.nnz > 0 && b.dense.valid && !(ops->debug_flags & M2L_DEBUG_NO_DENSE)) {
-        constexpr int prec = KIND == TC_TF32 ? M2L_TF32 : KIND == TC_BF16X3 ? M2L_BF16X3 : M2L_TF32X3;
+    if (b.nnz > 0 && b.dense.valid && !(ops->debug_flags & M2L_DEBUG_NO_DENSE))
         return launch_tc_dense(ops, b.dense, prec, in, out, out_fp64, scale, s);
-    }
     const int katoms = tc_katoms<KIND>(n3);
     const int cols_part = tc_a_cols_part<KIND>(katoms);
     const size_t a_bytes = (size_t)Tr::nparts * 128 * cols_part * sizeof(uint32_t);
@@ -621,7 +618,7 @@ m2l_status launch_big(const m2l_ops *ops, const Buckets &b, Layout &L, const flo
                                                  L.b.as<int16_t>(), in, out_fp64 ? nullptr : (float *)out,
                                                  out_fp64 ? (double *)out : nullptr, n3, (float)scale, ops->d_status,
                                                  (ops->debug_flags & M2L_DEBUG_STALL_PRODUCER) ? 1 : 0, kNumSym,
-                                                 nullptr, nullptr);
+                                                 nullptr, nullptr, n3, nullptr);
     M2L_LAUNCH_CHECK("tc_big_kernel");
     return M2L_OK;
 }
@@ -661,7 +658,7 @@ m2l_status launch_big_general(int N, int ncls, const int *tile_start, const int2
     const long tiles_bound = (long)(nnz + NT - 1) / NT + ncls;
     if (grid > tiles_bound) grid = tiles_bound;
     kern<<<(int)grid, big_threads(kGeneralEG), C::SMEM, s>>>(rec, class_off, img, tinv, in, out, nullptr, N, 1.0f,
-                                                             status, 0, ncls, tile_start, nullptr);
+                                                             status, 0, ncls, tile_start, nullptr, N, nullptr);
     M2L_LAUNCH_CHECK("tc_big_kernel");
     return M2L_OK;
 }

@@ -101,7 +101,8 @@ m2l_status launch_group_cfg(const TcGroup &g, int *status, cudaStream_t s)
     kern<<<grid, big_threads(EG), C::SMEM, s>>>(g.rec.as<int2>(), g.class_off.as<int>(), g.img.as<uint8_t>(),
                                                 g.tinv.as<int16_t>(), g.in_cat.as<float>(), g.out_cat.as<float>(),
                                                 nullptr, g.n3, 1.0f, status, 0, g.ncls,
-                                                NT == 32 ? g.ts32.as<int>() : g.ts64.as<int>(), g.img_of.as<int>());
+                                                NT == 32 ? g.ts32.as<int>() : g.ts64.as<int>(), g.img_of.as<int>(),
+                                                g.n3, nullptr);
     M2L_LAUNCH_CHECK("tc_big_kernel");
     return M2L_OK;
 }

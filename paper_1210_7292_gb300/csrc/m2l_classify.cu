@@ -308,6 +308,9 @@ static m2l_status bucket(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const 
     b.have_rec = true;
     const int nseg = (nnz + kSegEntries - 1) / kSegEntries;
     if ((st = b.rec.ensure((size_t)(nnz > 0 ? nnz : 1) * sizeof(int2))) != M2L_OK) return st;
+    // low-rank operators: the first-pass products of the tensor-core apply, one row per record
+    if (ops->eps > 0 && nnz > 0)
+        if ((st = b.lrz.ensure((size_t)nnz * kLrRankPad * sizeof(float))) != M2L_OK) return st;
     if (nnz > 0 && dense_eligible(ops, ntgt, nnz)) {
         // full level: the dense classification only; the operator buckets are derived
         // from it if a bucketed kernel is asked for (their buffers are allocated now)

@@ -117,6 +117,7 @@ struct Buckets {
     DevBuf class_off;  // int32 [18]: start of bucket p at [p], [16] = valid total, [17] = nnz
     // adjoint: transposed list (scratch)
     DevBuf t_off, t_src, t_cursor;
+    DevBuf lrz;           // float [nnz][128]: first-pass products of the tensor-core low-rank apply
     DenseBuckets dense;   // filled instead of the buckets for full levels that the dense kernel serves
     mutable bool have_rec = true;   // rec/class_off hold the buckets (else derived from dense on demand)
     int nnz = 0;
@@ -151,6 +152,7 @@ struct m2l_ops {
     m2l::DevBuf U64, V64;     // double [16][n3][rmax] (low rank; zero-padded columns)
     m2l::Layout simt64, simt32, lr64, lr32, tc_tf32, tc_bf16x3, tc_tf32x3;
     m2l::Layout tcd_tf32, tcd_bf16x3, tcd_tf32x3;   // per-slot operator images of the dense kernel
+    m2l::Layout lrtc_tf32, lrtc_bf16x3, lrtc_tf32x3; // low-rank factor images of the tensor-core apply
     mutable m2l::Buckets ws;  // workspace of m2l_apply_level
     mutable double ws_scale = 1.0;  // scale of the level last classified into ws
     int lowrank_method = 0;   // 0: truncated SVD, 1: ACA + truncated SVD
@@ -201,6 +203,12 @@ m2l_status dense_classify(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const
 m2l_status dense_prepare(const m2l_ops *ops, int precision, cudaStream_t s);
 m2l_status launch_tc_dense(const m2l_ops *ops, const DenseBuckets &d, int precision, const float *in, void *out,
                            int out_fp64, double scale, cudaStream_t s);
+// Low-rank products on the tensor cores (m2l_lowrank_tc.cu), two passes of the
+// large-order kernel; eps > 0, ell 5-7, ranks <= 128.
+constexpr int kLrRankPad = 128;
+m2l_status launch_tc_lowrank(const m2l_ops *ops, const Buckets &b, int precision, const float *in, void *out,
+                             int out_fp64, double scale, cudaStream_t s);
+
 // Fill b.rec / b.class_off from the dense classification if they are not built
 // (stream-ordered, no allocation).
 m2l_status ensure_records(const m2l_ops *ops, const Buckets &b, cudaStream_t s);

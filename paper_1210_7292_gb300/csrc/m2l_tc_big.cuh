@@ -60,12 +60,20 @@ struct BigCfg {
 // (every other tile), each with its own transpose buffer and named barrier.
 constexpr int big_threads(int eg) { return (kBigEpiWarp0 + 4 * eg) * 32; }
 
-template <int KIND, int MT, int KA, int NT_ = kBigNT, int EG_ = 1>
+// MODE 0: the M2L of Alg. 2 (gather + permute, product, un-permute + scatter-add).
+// MODE 1: first low-rank pass, Z = V_p^T W_p (Eq. (20)): gather + permute as in
+//         mode 0, the product's columns stored unpermuted to out_f32 at the
+//         record's position (n3 values per record, no accumulation).
+// MODE 2: second low-rank pass, F = (U_p Sigma_p) Z: the column of a record is
+//         row col0 + c of mp (n_in values, gathered through sinv_prod, an
+//         identity table), un-permute + scatter-add as in mode 0.
+template <int KIND, int MT, int KA, int NT_ = kBigNT, int EG_ = 1, int MODE = 0>
 __global__ void __launch_bounds__(big_threads(EG_), 1)
 tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, const uint8_t *__restrict__ a_img,
               const int16_t *__restrict__ sinv_pad, const float *__restrict__ mp, float *__restrict__ out_f32,
               double *__restrict__ out_f64, int n3, float scale, int *status, int stall_first_stage, int ncls,
-              const int *__restrict__ tile_start_g, const int *__restrict__ img_of_class)
+              const int *__restrict__ tile_start_g, const int *__restrict__ img_of_class, int n_in,
+              const int16_t *__restrict__ sinv_prod)
 {
     // n3 is the vector length; with tile_start_g (device, ncls + 1 tile offsets)
     // the classes are ncls operators of a_img, else the 16 of the symmetry method.
@@ -162,8 +170,8 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
                 const int c = it / CPC, j = it % CPC;
                 const bool live = (it < NT * CPC) && (c < nc);
                 const int2 r = live ? prec[c] : make_int2(0, 0);
-                const float *w = mp + (size_t)r.x * n3;
-                const int16_t *si = sinv_pad + rec_g(r.y) * C::KPAD + EPC * j;
+                const float *w = mp + (size_t)(MODE == 2 ? col0 + c : r.x) * n_in;
+                const int16_t *si = (sinv_prod ? sinv_prod : sinv_pad) + rec_g(r.y) * C::KPAD + EPC * j;
                 int16_t idx[EPC];
                 if (live) {
                     if constexpr (EPC == 4) {
@@ -320,7 +328,9 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
             if (EG == 2 && buf != grp) continue;
             if (a < NT) {
                 const int2 r = (a < nc) ? __ldg(rec + col0 + a) : make_int2(0, 0);
-                e_goff[a] = rec_g(r.y) * C::KPAD;
+                // un-permutation table rows: K-padded for the M2L, row-padded (MT tiles)
+                // for the second low-rank pass, whose K is the rank
+                e_goff[a] = rec_g(r.y) * (MODE == 2 ? MT * 128 : C::KPAD);
                 e_tgt[a] = (a < nc) ? rec_tgt(r.y) : -1;
             }
             const bool ok = mbar_wait(tfull + buf, kb & 1, abort_flag, status);
@@ -337,12 +347,22 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
                         mbar_arrive(tempty + buf);
                     }
                     const int row = mt * 128 + 32 * q + lane;
+                    if constexpr (MODE == 1) {
+                        // Z column of the record, unpermuted, no accumulation
+                        if (row < n3) {
+#pragma unroll
+                            for (int jj = 0; jj < 16; ++jj)
+                                if (16 * ch + jj < nc) out_f32[(size_t)(col0 + 16 * ch + jj) * n3 + row] = v[jj];
+                        }
+                        continue;
+                    }
                     if (row < n3) {
 #pragma unroll
                         for (int jj = 0; jj < 16; ++jj)
                             sF[jj * FS + __ldg(sinv_pad + e_goff[16 * ch + jj] + row)] = v[jj];
                     }
                 }
+                if constexpr (MODE == 1) continue;
                 named_bar_sync(bar_id, 128);
                 int tg[16];
 #pragma unroll

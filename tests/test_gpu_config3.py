@@ -7,7 +7,9 @@ Level 6 is applied with the low-rank and the full-rank operators in FP64 and
 FP32 on the CUDA cores and compared on sampled targets with the oracle's
 per-pair truncated operators; the relative L2 error of each precision
 against the FP64 oracle is printed; the full-rank operators also run in the
-tensor-core precisions (TF32, split BF16, split TF32 with FP32 accumulation)."""
+tensor-core precisions (TF32, split BF16, split TF32 with FP32 accumulation),
+and so do the low-rank factors (two tensor-core passes, Z = V_p^T W_p then
+(U_p Sigma_p) Z), against the oracle's truncated operators."""
 import numpy as np
 import pytest
 
@@ -81,3 +83,42 @@ def test_config3_level6_lowrank_and_full(m2l):
         assert errs[("full", prec)] < TOL[prec], (prec, errs[("full", prec)])
     print("config3 tensor-core rel L2 vs FP64 oracle:",
           {p: "%.2e" % errs[("full", p)] for p in ("tf32", "bf16x3", "tf32x3")})
+    # the tensor-core precisions on the low-rank factors (two passes)
+    for prec in ("tf32", "bf16x3", "tf32x3"):
+        loc = torch.zeros(len(cells), ell ** 3, dtype=torch.float64, device=device())
+        m2l.m2l_apply_level(ops_lr, lv, torch.from_numpy(w).to(device(), torch.float32), loc, prec,
+                            locals_fp64=True)
+        m2l.m2l_sync_status(ops_lr)
+        errs[("lowrank", prec)] = oracle.rel_l2(loc[idx].cpu().numpy(), ref_lr)
+        assert errs[("lowrank", prec)] < TOL[prec], (prec, errs[("lowrank", prec)])
+    print("config3 low-rank tensor-core rel L2 vs FP64 oracle:",
+          {p: "%.2e" % errs[("lowrank", p)] for p in ("tf32", "bf16x3", "tf32x3")})
+
+
+@pytest.mark.parametrize("ell,kind,level,keep,eps", [(5, 0, 3, 1.0, 1e-5), (6, 1, 3, 0.7, 1e-6), (5, 2, 4, 0.4, 1e-4)])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "tf32"])
+def test_lowrank_tensor_cores_match_oracle(m2l, ell, kind, level, keep, eps, prec):
+    """The low-rank tensor-core apply on whole levels (ell 5-6, three kernels,
+    full and pruned levels, the adjoint too) against the oracle's truncated
+    operators."""
+    from gpu_helpers import KIND_C, gpu_ops, make_level, pruned_cells
+    from paper_1210_7292_gb300 import synth
+    cells = synth.full_grid(level) if keep == 1.0 else pruned_cells(level, keep, seed=ell + 13 * level)
+    w = synth.gaussian_vectors(len(cells), ell ** 3, seed=91 + ell)
+    lv = make_level(m2l, cells, level)
+    ops = gpu_ops(m2l, ell, kind, level, eps=eps)
+    off, src = oracle.interaction_lists(cells, cells)
+    K, _ = oracle.lowrank_operator_table(oracle.operator_table(ell, kind, KIND_C[kind], level), eps)
+    ref = oracle.m2l_apply(K, cells, cells, off, src, w)
+    loc = torch.zeros(len(cells), ell ** 3, dtype=torch.float32, device=device())
+    m2l.m2l_apply_level(ops, lv, torch.from_numpy(w).to(device(), torch.float32), loc, prec)
+    m2l.m2l_sync_status(ops)
+    err = oracle.rel_l2(loc.double().cpu().numpy(), ref)
+    assert err < TOL[prec], err
+    ref_adj = oracle.m2l_apply_adjoint(K, cells, cells, off, src, w, len(cells))
+    adj = torch.zeros_like(loc)
+    m2l.m2l_apply_level_adjoint(ops, lv, torch.from_numpy(w).to(device(), torch.float32), adj, prec)
+    m2l.m2l_sync_status(ops)
+    err_adj = oracle.rel_l2(adj.double().cpu().numpy(), ref_adj)
+    assert err_adj < TOL[prec], err_adj
+    print("low-rank %s ell=%d kind=%d level=%d: rel L2 %.2e, adjoint %.2e" % (prec, ell, kind, level, err, err_adj))
