@@ -762,8 +762,9 @@ def dfmm_m2l(m2l, device, mm, reps=5):
 def config3_levels(m2l, device, reps=5):
     """The mixed-precision workload (4 M points on the ellipsoid (1, 0.5, 0.25),
     ell = 7, 1/r^4, SVD at eps = 1e-7), levels 4-6: every level in the low-rank
-    operators (FP64, FP32 on the CUDA cores) and in the full-rank ones (FP64, FP32,
-    TF32, BF16x3, TF32x3), timed per level with its lists classified once, and the
+    operators (FP64, FP32 on the CUDA cores; TF32, BF16x3, TF32x3 on the tensor
+    cores, two passes) and in the full-rank ones (FP64, FP32, TF32, BF16x3,
+    TF32x3), timed per level with its lists classified once, and the
     error of each against the FP64 full-rank result.  GFLOP/s counts the products
     each one performs (full: 2 ell^6; low rank: 4 r_p ell^3 per interaction)."""
     import numpy as np
@@ -790,7 +791,8 @@ def config3_levels(m2l, device, reps=5):
         res = {"cells": len(cells), "interactions": lv.nnz}
         ref = None
         for name, prec in (("full", "fp64"), ("lowrank", "fp64"), ("lowrank", "fp32"), ("full", "fp32"),
-                           ("full", "tf32"), ("full", "bf16x3"), ("full", "tf32x3")):
+                           ("full", "tf32"), ("full", "bf16x3"), ("full", "tf32x3"),
+                           ("lowrank", "tf32"), ("lowrank", "bf16x3"), ("lowrank", "tf32x3")):
             win = w64 if prec == "fp64" else w64.float()
             loc = torch.zeros(len(cells), n3, dtype=torch.float64, device=device)
             fp64_out = prec != "fp64"
