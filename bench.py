@@ -1258,8 +1258,9 @@ def run_dfmm_apply_only(args):
 
 def run_config3_apply_only(args):
     """Level 6 of the mixed-precision workload (4M points on the ellipsoid, ell
-    = 7, 1/r^4), full-rank operators, three applies in --config3-precision:
-    for profiler captures of the large-order kernel."""
+    = 7, 1/r^4), full-rank operators (or the SVD factors at eps = 1e-7 with
+    --config3-lowrank), three applies in --config3-precision: for profiler
+    captures of the large-order kernel."""
     import torch
     import __graft_entry__ as g
     g.build()
@@ -1271,7 +1272,7 @@ def run_config3_apply_only(args):
     ijk = torch.from_numpy(cells).to(device)
     off, src = m2l.m2l_build_lists(ijk, ijk)
     lv = m2l.Level(2.0 / (1 << L), ijk, ijk, off, src, L)
-    ops = m2l.m2l_precompute(m2l.M2L_K_INV_R4, ell)
+    ops = m2l.m2l_precompute(m2l.M2L_K_INV_R4, ell, 1e-7 if args.config3_lowrank else 0.0)
     plan = m2l.m2l_plan_create(ops, lv)
     prec = args.config3_precision
     w = torch.from_numpy(synth.gaussian_vectors(len(cells), ell ** 3, seed=33 + L)).to(device, torch.float32)
@@ -1283,7 +1284,8 @@ def run_config3_apply_only(args):
         m2l.m2l_plan_apply(plan, w, loc, prec)
         e.record()
         torch.cuda.synchronize()
-        log("config-3 level-6 apply (%s, %d interactions): %.3f ms" % (prec, lv.nnz, s.elapsed_time(e)))
+        log("config-3 level-6 apply (%s%s, %d interactions): %.3f ms"
+            % (prec, ", low rank" if args.config3_lowrank else "", lv.nnz, s.elapsed_time(e)))
     m2l.m2l_sync_status(ops)
     return 0
 
@@ -1307,6 +1309,8 @@ def main():
                     help="run three directional level-5 apply launches only (for profiler captures)")
     ap.add_argument("--config3-apply-only", action="store_true",
                     help="run three level-6 applies of the mixed-precision workload only (for profiler captures)")
+    ap.add_argument("--config3-lowrank", action="store_true",
+                    help="with --config3-apply-only: the per-operator SVD factors at eps = 1e-7")
     ap.add_argument("--config3-precision", default="bf16x3", choices=["fp32", "tf32", "bf16x3", "tf32x3"],
                     help="precision of --config3-apply-only")
     ap.add_argument("--dfmm-precision", default="fp32", choices=["fp64", "fp32", "tf32", "bf16x3", "tf32x3"],
