@@ -27,8 +27,9 @@ What it computes, each function citing its source:
 Readings of the paper taken where it is silent or garbled (each stated where
 it is used): roots in ascending order; P_t oriented so that
 K_t[a, b] = K_{p(t)}[sigma_t(a), sigma_t(b)]; ties of |t_i| broken by a stable
-sort (lower axis first); SVD truncated at the smallest r with
-s_{r+1} <= eps * s_1.
+sort (lower axis first); SVD truncated at the smallest r whose Frobenius
+tail is within eps of the Frobenius norm, sum_{i>r} s_i^2 <= eps^2 sum s_i^2
+(the spectral reading s_{r+1} <= eps s_1 is an option).
 """
 from __future__ import annotations
 
@@ -324,24 +325,46 @@ def operator_table(ell: int, kind: int, c: float, level: int, lo: float = -1.0,
     return ops
 
 
-def truncation_rank(s: np.ndarray, eps: float) -> int:
-    """Smallest r with s_{r+1} <= eps * s_1 (reading of "accuracy eps" for Eq. (20))."""
+FROBENIUS, SPECTRAL = "frobenius", "spectral"
+
+
+def truncation_rank(s: np.ndarray, eps: float, criterion: str = FROBENIUS) -> int:
+    """Truncation rank at "accuracy eps" (Eq. (20) and Sec. 4.1), s descending.
+
+    frobenius: the smallest r with sum_{i>r} s_i^2 <= eps^2 sum_i s_i^2, i.e.
+      |K - K_r|_F <= eps |K|_F.  With it the paper's printed per-level costs of
+      SA and SArcmp (Sec. 5.2, bbFMM, prolate sphere, Acc 9) come out exactly.
+    spectral: the smallest r with s_{r+1} <= eps s_1, i.e. |K - K_r|_2 <= eps |K|_2.
+    """
+    s = np.asarray(s, dtype=np.float64)
+    n = len(s)
     if eps <= 0.0:
-        return len(s)
-    return int(np.count_nonzero(s > eps * s[0]))
+        return n
+    if criterion == SPECTRAL:
+        return int(np.count_nonzero(s > eps * s[0]))
+    if criterion != FROBENIUS:
+        raise ValueError("unknown truncation criterion %r" % (criterion,))
+    # tail[r] = sum_{i >= r} s_i^2 (0-based), summed from the smallest value up
+    tail = np.zeros(n + 1)
+    for i in range(n - 1, -1, -1):
+        tail[i] = tail[i + 1] + s[i] * s[i]
+    for r in range(n + 1):
+        if tail[r] <= eps * eps * tail[0]:
+            return r
+    return n
 
 
-def lowrank(K: np.ndarray, eps: float):
+def lowrank(K: np.ndarray, eps: float, criterion: str = FROBENIUS):
     """Truncated SVD K ~ U_t V_t^T of Eq. (20), U_t = U_r Sigma_r, V_t = V_r.
 
     Returns (U_t, V_t, rank).
     """
     U, s, Vt = np.linalg.svd(K)
-    r = truncation_rank(s, eps)
+    r = truncation_rank(s, eps, criterion)
     return U[:, :r] * s[None, :r], Vt[:r, :].T.copy(), r
 
 
-def lowrank_operator_table(ops: np.ndarray, eps: float):
+def lowrank_operator_table(ops: np.ndarray, eps: float, criterion: str = FROBENIUS):
     """Replace every stored operator by its rank-r_t truncation U_t V_t^T.
 
     Returns (table, ranks) where ranks[slot] is r_t (0 for unused slots).
@@ -350,7 +373,7 @@ def lowrank_operator_table(ops: np.ndarray, eps: float):
     ranks = np.zeros(343, dtype=np.int64)
     for t in transfer_vectors():
         s = t_slot(t)
-        U, V, r = lowrank(ops[s], eps)
+        U, V, r = lowrank(ops[s], eps, criterion)
         out[s] = U @ V.T
         ranks[s] = r
     return out, ranks
@@ -417,41 +440,43 @@ def aca(K: np.ndarray, eps_aca: float, kmax: int = None, return_pivots: bool = F
     return (U, V, piv) if return_pivots else (U, V)
 
 
-def aca_lowrank(K: np.ndarray, eps: float):
-    """ACA at eps_ACA = ACA_EPS_FACTOR eps, then the truncated SVD of the
-    approximant (QR of both factors, SVD of the small core), truncated with the
-    criterion of Eq. (20).  Returns (U_t = U_r Sigma_r, V_t, rank, aca_terms)."""
-    Ua, Va = aca(K, ACA_EPS_FACTOR * eps)
+def aca_lowrank(K: np.ndarray, eps: float, criterion: str = FROBENIUS, eps_factor: float = None):
+    """ACA at eps_ACA = eps_factor eps (default ACA_EPS_FACTOR), then the
+    truncated SVD of the approximant (QR of both factors, SVD of the small
+    core), truncated with the criterion of Eq. (20).
+    Returns (U_t = U_r Sigma_r, V_t, rank, aca_terms)."""
+    Ua, Va = aca(K, (ACA_EPS_FACTOR if eps_factor is None else eps_factor) * eps)
     Qu, Ru = np.linalg.qr(Ua)
     Qv, Rv = np.linalg.qr(Va)
     W, s, Zt = np.linalg.svd(Ru @ Rv.T)
-    r = max(1, truncation_rank(s, eps))
+    r = max(1, truncation_rank(s, eps, criterion))
     return (Qu @ W[:, :r]) * s[None, :r], Qv @ Zt[:r, :].T, r, Ua.shape[1]
 
 
 # --------------------------------------------------------------------------
 # single low-rank approximation (SA) and its recompression (SArcmp), Sec. 4.1
 # --------------------------------------------------------------------------
-def sa_factors(ops: np.ndarray, eps: float):
-    """SA of Sec. 4.1, Eqs. (17)-(18), for the 316 operators of a level.
+def sa_factors(ops: np.ndarray, eps: float, criterion: str = FROBENIUS, ts=None):
+    """SA of Sec. 4.1, Eqs. (17)-(18), for the operators of a level's T.
 
-    The operators of T are joined as a row K_row = [K_t1, ..., K_t316] and as a
-    column K_col = [K_t1; ...; K_t316] (T in the order of transfer_vectors());
+    The operators of T (default: all 316, in the order of transfer_vectors())
+    are joined as a row K_row = [K_t1, ..., K_t|T|] and as a column
+    K_col = [K_t1; ...; K_t|T|];
     K_row ~ U Sigma V^*, K_col ~ A Gamma B^* by truncated SVDs.  The paper gives
     one rank r for both; it is read here as the larger of the two truncation
-    ranks at accuracy eps (same spectral criterion as Eq. (20)).  Then
+    ranks at accuracy eps (same criterion as Eq. (20)).  Then
     K_t ~ U C_t B^* with C_t = U^* K_t B.
 
     Returns dict: U [n3, r], B [n3, r], C [343, r, r] at the t-slots (zeros
     elsewhere), r, the singular values of K_row and K_col, and, for the pins,
     Sigma V_t^* B and U^* A_t Gamma (the paper's two other forms of C_t).
     """
-    ts = transfer_vectors()
+    ts = transfer_vectors() if ts is None else list(ts)
     Ks = [ops[t_slot(t)] for t in ts]
     n3 = Ks[0].shape[0]
     Urow, s_row, Vh_row = np.linalg.svd(np.concatenate(Ks, axis=1), full_matrices=False)
     Acol, s_col, Bh_col = np.linalg.svd(np.concatenate(Ks, axis=0), full_matrices=False)
-    r = max(truncation_rank(s_row, eps), truncation_rank(s_col, eps))
+    r = max(truncation_rank(s_row, eps, criterion), truncation_rank(s_col, eps, criterion))
     U, B = Urow[:, :r], Bh_col[:r, :].T
     C = np.zeros((343, r, r))
     C_sv = np.zeros((343, r, r))
@@ -465,20 +490,20 @@ def sa_factors(ops: np.ndarray, eps: float):
             "C_a_gamma": C_ag}
 
 
-def sa_recompress(C: np.ndarray, r: int, eps: float):
+def sa_recompress(C: np.ndarray, r: int, eps: float, criterion: str = FROBENIUS, ts=None):
     """SArcmp, Eq. (19) of Sec. 4.1.1: each C_t ~ Ubar_t Vbar_t^* with rank
-    r_t (same criterion at accuracy eps, relative to C_t's largest singular
-    value), kept only when r_t < r / 2; otherwise C_t stays as it is.
+    r_t (same criterion at accuracy eps, relative to C_t's own singular
+    values), kept only when r_t < r / 2; otherwise C_t stays as it is.
 
     Returns (table [343, r, r] of the represented C_t, ranks [343]: r_t, or r
     where C_t is kept whole, 0 at unused slots).
     """
     out = np.zeros_like(C)
     ranks = np.zeros(343, dtype=np.int64)
-    for t in transfer_vectors():
+    for t in (transfer_vectors() if ts is None else ts):
         sl = t_slot(t)
         u, sv, vh = np.linalg.svd(C[sl])
-        rt = truncation_rank(sv, eps)
+        rt = truncation_rank(sv, eps, criterion)
         if 2 * rt < r:
             out[sl] = (u[:, :rt] * sv[None, :rt]) @ vh[:rt, :]
             ranks[sl] = rt
@@ -488,13 +513,13 @@ def sa_recompress(C: np.ndarray, r: int, eps: float):
     return out, ranks
 
 
-def sa_operator_table(ops: np.ndarray, eps: float, recompress: bool = False):
+def sa_operator_table(ops: np.ndarray, eps: float, recompress: bool = False, criterion: str = FROBENIUS):
     """The SA (or SArcmp) operators U C_t B^* at the t-slots, for m2l_apply.
 
     Returns (table [343, n3, n3], sa dict, recompression ranks or None).
     """
-    sa = sa_factors(ops, eps)
-    C, ranks = (sa_recompress(sa["C"], sa["r"], eps) if recompress else (sa["C"], None))
+    sa = sa_factors(ops, eps, criterion)
+    C, ranks = (sa_recompress(sa["C"], sa["r"], eps, criterion) if recompress else (sa["C"], None))
     out = np.zeros_like(ops)
     for t in transfer_vectors():
         sl = t_slot(t)
@@ -800,7 +825,8 @@ def fmm_at_samples(up: UpwardPass, kind: int, c: float, locals_by_level: dict,
     return out
 
 
-def fmm_oracle_locals(up: UpwardPass, kind: int, c: float, eps: float = 0.0) -> dict:
+def fmm_oracle_locals(up: UpwardPass, kind: int, c: float, eps: float = 0.0,
+                      criterion: str = FROBENIUS) -> dict:
     """M2L locals of every level 2..leaf by the oracle (directly assembled operators)."""
     out = {}
     for L in range(2, up.leaf_level + 1):
@@ -808,6 +834,6 @@ def fmm_oracle_locals(up: UpwardPass, kind: int, c: float, eps: float = 0.0) -> 
         off, src = interaction_lists(cells, cells)
         ops = operator_table(up.ell, kind, c, L, up.lo, up.domain_width)
         if eps > 0:
-            ops, _ = lowrank_operator_table(ops, eps)
+            ops, _ = lowrank_operator_table(ops, eps, criterion)
         out[L] = m2l_apply(ops, cells, cells, off, src, W)
     return out
