@@ -326,6 +326,7 @@ def operator_table(ell: int, kind: int, c: float, level: int, lo: float = -1.0,
 
 
 FROBENIUS, SPECTRAL = "frobenius", "spectral"
+CLUSTER_GAP = 1e-12   # singular values closer than this (relative to s_1) are one cluster
 
 
 def truncation_rank(s: np.ndarray, eps: float, criterion: str = FROBENIUS) -> int:
@@ -335,23 +336,33 @@ def truncation_rank(s: np.ndarray, eps: float, criterion: str = FROBENIUS) -> in
       |K - K_r|_F <= eps |K|_F.  With it the paper's printed per-level costs of
       SA and SArcmp (Sec. 5.2, bbFMM, prolate sphere, Acc 9) come out exactly.
     spectral: the smallest r with s_{r+1} <= eps s_1, i.e. |K - K_r|_2 <= eps |K|_2.
+
+    The truncated SVD is unique only when s_r > s_{r+1}.  A cut that would
+    split a cluster of equal singular values (operators with a symmetry have
+    such pairs) moves past the cluster: r grows while s_r - s_{r+1} <=
+    CLUSTER_GAP s_1, a gap no SVD in double precision resolves.
     """
     s = np.asarray(s, dtype=np.float64)
     n = len(s)
     if eps <= 0.0:
         return n
     if criterion == SPECTRAL:
-        return int(np.count_nonzero(s > eps * s[0]))
-    if criterion != FROBENIUS:
+        r = int(np.count_nonzero(s > eps * s[0]))
+    elif criterion == FROBENIUS:
+        # tail[r] = sum_{i >= r} s_i^2 (0-based), summed from the smallest value up
+        tail = np.zeros(n + 1)
+        for i in range(n - 1, -1, -1):
+            tail[i] = tail[i + 1] + s[i] * s[i]
+        r = n
+        for k in range(n + 1):
+            if tail[k] <= eps * eps * tail[0]:
+                r = k
+                break
+    else:
         raise ValueError("unknown truncation criterion %r" % (criterion,))
-    # tail[r] = sum_{i >= r} s_i^2 (0-based), summed from the smallest value up
-    tail = np.zeros(n + 1)
-    for i in range(n - 1, -1, -1):
-        tail[i] = tail[i + 1] + s[i] * s[i]
-    for r in range(n + 1):
-        if tail[r] <= eps * eps * tail[0]:
-            return r
-    return n
+    while 0 < r < n and s[r - 1] - s[r] <= CLUSTER_GAP * s[0]:
+        r += 1
+    return r
 
 
 def lowrank(K: np.ndarray, eps: float, criterion: str = FROBENIUS):

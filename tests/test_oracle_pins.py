@@ -313,6 +313,11 @@ def test_eckart_young_truncation():
     assert o.truncation_rank(sv, 0.0099, o.SPECTRAL) == 3
     with pytest.raises(ValueError):
         o.truncation_rank(sv, 0.1, "nuclear")
+    # a cut inside a cluster of equal values moves past it: tails^2 of
+    # (1, .5, .5, .1) are 1.51, .51, .26, .01; eps^2 1.51 = .3058 puts the cut at 2
+    assert o.truncation_rank(np.array([1.0, 0.5, 0.5, 0.1]), 0.45, o.FROBENIUS) == 3
+    assert o.truncation_rank(np.array([1.0, 0.5, 0.49, 0.1]), 0.45, o.FROBENIUS) == 2
+    assert o.truncation_rank(np.array([1.0, 0.5, 0.5, 0.1]), 0.3, o.SPECTRAL) == 3
 
 
 def _prolate_column_lists(level):
@@ -604,7 +609,9 @@ def test_aca_interpolates_its_pivot_rows_and_columns():
 @pytest.mark.parametrize("criterion", ["spectral", "frobenius"])
 @pytest.mark.parametrize("ell,kind,eps", [(5, 0, 1e-5), (7, 1, 1e-7), (6, 2, 1e-6), (3, 0, 1e-3)])
 def test_aca_then_svd_gives_the_svd_ranks(ell, kind, eps, criterion):
-    """Sec. 5: ACA followed by a truncated SVD ends with the same ranks as the SVD;
+    """Sec. 5: ACA followed by a truncated SVD ends with the same ranks as the SVD
+    (where the SVD's cut moved past a cluster of equal singular values, which
+    the ACA approximant no longer holds equal, by that cluster at most);
     the error stays within the truncation bound of the ACA approximant S plus
     the ACA residual, |K - U V^T| <= |K - S| + eps |S| (triangle inequality; the
     2-norm for the spectral reading, the Frobenius norm for the Frobenius one),
@@ -617,7 +624,8 @@ def test_aca_then_svd_gives_the_svd_ranks(ell, kind, eps, criterion):
         K = o.operator_for_t(ell, kind, c, 3, t)
         _, _, r = o.lowrank(K, eps, criterion)
         U, V, ra, k = o.aca_lowrank(K, eps, criterion)
-        assert ra == r, (t, r, ra)
+        sk = np.linalg.svd(K, compute_uv=False)
+        assert ra == r or (ra < r and sk[ra - 1] - sk[r - 1] <= o.CLUSTER_GAP * sk[0]), (t, r, ra)
         Ua, Va = o.aca(K, o.ACA_EPS_FACTOR * eps)
         S = Ua @ Va.T
         res = np.linalg.norm(K - S, nrm)
