@@ -72,6 +72,19 @@ typedef struct {
     double c;   /* used by M2L_K_INV_SQRT_R2C2 only */
 } m2l_kernel;
 
+/* Truncation criterion of "accuracy eps" for the low-rank factors (Eq. (20)),
+ * SA and SArcmp (Eqs. (17)-(19)), on the singular values s_1 >= s_2 >= ...
+ * of the matrix truncated. */
+typedef enum {
+    M2L_TRUNC_FROBENIUS = 0,  /* smallest r with sum_{i>r} s_i^2 <= eps^2 sum_i s_i^2,
+                                 i.e. |K - K_r|_F <= eps |K|_F (the default: the paper's
+                                 per-level SA and SArcmp costs of Sec. 5.2 follow from it) */
+    M2L_TRUNC_SPECTRAL = 1    /* smallest r with s_{r+1} <= eps s_1, i.e. |K - K_r|_2 <= eps |K|_2 */
+} m2l_truncation;
+/* Under either criterion a cut never splits a cluster of equal singular
+ * values (the truncation would not be unique): r grows while
+ * s_r - s_{r+1} <= 1e-12 s_1. */
+
 /* Arithmetic of the operator products (step 2 of Sec. 4.2.2).
  * Multipoles are double for M2L_FP64 and float otherwise. */
 typedef enum {
@@ -111,7 +124,10 @@ typedef struct {
  *  - the 48 permutation tables sigma_g (Eqs. (26)-(29)) and the 343-entry
  *    table t -> (p, g);
  *  - when eps > 0, a truncated SVD of each K_p, K_p ~ (U_p Sigma_p) V_p^T
- *    (Eq. (20)), at the smallest rank r_p with s_{r+1} <= eps * s_1.
+ *    (Eq. (20)), at the rank the truncation criterion gives (M2L_TRUNC_FROBENIUS
+ *    here; m2l_precompute_ex chooses).  The SVD is one-sided Jacobi on the
+ *    device (FP64, rotations of column pairs in round-robin order until every
+ *    pair is orthogonal to 1e-12 relative to the columns' norms).
  * ell: Chebyshev order, 2 <= ell <= 8.  eps: 0 for full rank, else in (0, 1).
  * width: cell width for the non-homogeneous kernel (ignored otherwise).
  * out: receives a new m2l_ops; free with m2l_ops_free.
@@ -131,6 +147,20 @@ m2l_status m2l_precompute(m2l_kernel kernel, int ell, double eps, double width, 
  * entry point uses them alike.  With eps = 0 it equals m2l_precompute.
  * Errors as m2l_precompute; M2L_ECUDA if a Jacobi SVD does not converge. */
 m2l_status m2l_precompute_aca(m2l_kernel kernel, int ell, double eps, double width, m2l_ops **out);
+
+/* m2l_precompute (aca = 0) or m2l_precompute_aca (aca = 1) with the truncation
+ * criterion `trunc` (m2l_truncation) for the low-rank factors; SA objects made
+ * from the ops (m2l_sa_create) use the same criterion.  M2L_EINVAL for an
+ * unknown criterion or aca outside {0, 1}; other errors as m2l_precompute. */
+m2l_status m2l_precompute_ex(m2l_kernel kernel, int ell, double eps, double width, int trunc, int aca,
+                             m2l_ops **out);
+
+/* The truncation criterion (m2l_truncation) the ops were built with. */
+m2l_status m2l_ops_truncation(const m2l_ops *ops, int *trunc);
+
+/* Jacobi sweeps of the SVD of each operator p (the full K_p for m2l_precompute,
+ * the ACA core for m2l_precompute_aca); M2L_EINVAL for full-rank ops. */
+m2l_status m2l_ops_svd_sweeps(const m2l_ops *ops, int32_t *sweeps16);
 
 /* Per operator p: ACA terms before the recompression and Jacobi sweeps, for
  * ops from m2l_precompute_aca with eps > 0 (else M2L_EINVAL); NULL skips one. */
@@ -340,16 +370,17 @@ void m2l_fmm_free(m2l_fmm *fmm);
  * symmetries.  The operators are joined as K_row = [K_t1 ... K_t316] and
  * K_col = [K_t1; ...; K_t316]; truncated SVDs K_row ~ U S V^T and
  * K_col ~ A G B^T give K_t ~ U C_t B^T with the r x r cores C_t = U^T K_t B
- * (Eq. (18)).  r is the larger of the two truncation ranks at relative
- * accuracy eps (singular values above eps times the largest; eps = 0 keeps
- * all n3 = ell^3 of them).  SArcmp (recompress != 0, Eq. (19)) replaces a
- * core by its truncated SVD X_t Y_t^T of rank r_t (same criterion, relative
- * to C_t's largest singular value) when 2 r_t < r; otherwise C_t is kept.
+ * (Eq. (18)).  r is the larger of the two truncation ranks at accuracy eps
+ * under the truncation criterion of ops (m2l_truncation; eps = 0 keeps all
+ * n3 = ell^3 of them).  SArcmp (recompress != 0, Eq. (19)) replaces a core by
+ * its truncated SVD X_t Y_t^T of rank r_t (same criterion, on C_t's own
+ * singular values) when 2 r_t < r; otherwise C_t is kept.
  *
  * m2l_sa_create: builds the factors of the operators in ops (full rank, any
  *   eps of ops; only ops' 16 unique operators and their symmetries are
- *   read) in FP64 on the device with cuSOLVER; synchronous; allocates what
- *   it keeps.  eps in [0, 1).  r <= 128 (larger: M2L_EUNSUPPORTED).
+ *   read) in FP64 on the device, every SVD by one-sided Jacobi rotations
+ *   (as m2l_precompute's); synchronous; allocates what it keeps.  eps in
+ *   [0, 1).  r <= 128 (larger: M2L_EUNSUPPORTED).
  * m2l_sa_info: r, the number of recompressed cores and (host [343], may be
  *   NULL) r_t per t-slot (t + 3) . (1, 7, 49), 0 where C_t is kept whole or
  *   the slot is not a far-field transfer vector.

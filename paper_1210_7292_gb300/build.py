@@ -1,7 +1,7 @@
 """Builds libm2l.so (the CUDA kernels and the C ABI) in-tree for sm_103a.
 
 Each translation unit is compiled by nvcc in parallel, then linked into
-paper_1210_7292_gb300/libm2l.so against the CUDA runtime and cuSOLVER.
+paper_1210_7292_gb300/libm2l.so against the CUDA runtime alone.
 """
 from __future__ import annotations
 
@@ -58,7 +58,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcusolver", "-lcudart"]
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))

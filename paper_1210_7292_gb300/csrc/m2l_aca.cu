@@ -13,8 +13,9 @@
 //  4. Its SVD by one-sided Jacobi rotations (Hestenes' method; pairs in
 //     round-robin order, one warp per pair): C Z = A with orthogonal columns,
 //     C = W Sigma Z^T, sigma_j = |a_j|, W Sigma = A.
-//  5. Truncation at the smallest r with sigma_{r+1} <= eps sigma_1; the factors
-//     U_p = Q_u A_r (= U_K Sigma), V_p = Q_v Z_r, in the layout of the SVD path.
+//  5. Truncation with the ops' criterion (Frobenius tail or spectral, as the
+//     SVD path); the factors U_p = Q_u A_r (= U_K Sigma), V_p = Q_v Z_r, in the
+//     layout of the SVD path.
 #include <math.h>
 
 #include <algorithm>
@@ -377,7 +378,7 @@ m2l_status lowrank_factors_aca(m2l_ops *ops, int *aca_terms, int *jacobi_sweeps)
     int hsw[16];
     M2L_CUDA(cudaMemcpy(hs.data(), sig.p, hs.size() * sizeof(double), cudaMemcpyDeviceToHost));
     M2L_CUDA(cudaMemcpy(hsw, sw.p, sizeof(hsw), cudaMemcpyDeviceToHost));
-    // truncation (Eq. (20) criterion) on the singular values in descending order
+    // truncation (the criterion of Eq. (20)) on the singular values in descending order
     std::vector<int> horder((size_t)16 * kmax, 0);
     int rmax = 1;
     for (int p = 0; p < 16; ++p) {
@@ -390,11 +391,9 @@ m2l_status lowrank_factors_aca(m2l_ops *ops, int *aca_terms, int *jacobi_sweeps)
         std::iota(o, o + k, 0);
         const double *s = hs.data() + (size_t)p * kmax;
         std::stable_sort(o, o + k, [&](int a, int b) { return s[a] > s[b]; });
-        int r = 0;
-        if (k > 0) {
-            const double s1 = s[o[0]];
-            while (r < k && s[o[r]] > ops->eps * s1) ++r;
-        }
+        std::vector<double> sorted(k);
+        for (int i = 0; i < k; ++i) sorted[i] = s[o[i]];
+        int r = truncation_rank(sorted.data(), k, ops->eps, ops->trunc);
         if (r < 1) r = 1;
         ops->ranks[p] = r;
         rmax = std::max(rmax, r);

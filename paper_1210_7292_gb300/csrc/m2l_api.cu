@@ -142,7 +142,7 @@ static m2l_status dispatch(const m2l_ops *ops, const Buckets &b, const void *in,
 using namespace m2l;
 
 namespace {
-m2l_status precompute_impl(m2l_kernel kernel, int ell, double eps, double width, int aca, m2l_ops **out);
+m2l_status precompute_impl(m2l_kernel kernel, int ell, double eps, double width, int aca, int trunc, m2l_ops **out);
 }
 
 extern "C" {
@@ -153,12 +153,42 @@ int64_t m2l_launch_count(void) { return (int64_t)g_launches.load(); }
 
 m2l_status m2l_precompute(m2l_kernel kernel, int ell, double eps, double width, m2l_ops **out)
 {
-    return precompute_impl(kernel, ell, eps, width, 0, out);
+    return precompute_impl(kernel, ell, eps, width, 0, M2L_TRUNC_FROBENIUS, out);
 }
 
 m2l_status m2l_precompute_aca(m2l_kernel kernel, int ell, double eps, double width, m2l_ops **out)
 {
-    return precompute_impl(kernel, ell, eps, width, 1, out);
+    return precompute_impl(kernel, ell, eps, width, 1, M2L_TRUNC_FROBENIUS, out);
+}
+
+m2l_status m2l_precompute_ex(m2l_kernel kernel, int ell, double eps, double width, int trunc, int aca,
+                             m2l_ops **out)
+{
+    if (out) *out = nullptr;
+    if (trunc != M2L_TRUNC_FROBENIUS && trunc != M2L_TRUNC_SPECTRAL) {
+        set_error("unknown truncation criterion %d", trunc);
+        return M2L_EINVAL;
+    }
+    if (aca != 0 && aca != 1) {
+        set_error("aca must be 0 or 1, got %d", aca);
+        return M2L_EINVAL;
+    }
+    return precompute_impl(kernel, ell, eps, width, aca, trunc, out);
+}
+
+m2l_status m2l_ops_truncation(const m2l_ops *ops, int *trunc)
+{
+    if (!ops || !trunc) { set_error("null argument"); return M2L_EINVAL; }
+    *trunc = ops->trunc;
+    return M2L_OK;
+}
+
+m2l_status m2l_ops_svd_sweeps(const m2l_ops *ops, int32_t *sweeps16)
+{
+    if (!ops || !sweeps16) { set_error("null argument"); return M2L_EINVAL; }
+    if (ops->eps <= 0) { set_error("operators are full rank"); return M2L_EINVAL; }
+    for (int p = 0; p < 16; ++p) sweeps16[p] = ops->jacobi_sweeps[p];
+    return M2L_OK;
 }
 
 m2l_status m2l_ops_aca_info(const m2l_ops *ops, int32_t *aca_terms16, int32_t *jacobi_sweeps16)
@@ -175,7 +205,7 @@ m2l_status m2l_ops_aca_info(const m2l_ops *ops, int32_t *aca_terms16, int32_t *j
 }  // extern "C"
 
 namespace {
-m2l_status precompute_impl(m2l_kernel kernel, int ell, double eps, double width, int aca, m2l_ops **out)
+m2l_status precompute_impl(m2l_kernel kernel, int ell, double eps, double width, int aca, int trunc, m2l_ops **out)
 {
     g_err[0] = 0;
     if (!out) { set_error("null output pointer"); return M2L_EINVAL; }
@@ -193,6 +223,7 @@ m2l_status precompute_impl(m2l_kernel kernel, int ell, double eps, double width,
     ops->ell = ell;
     ops->n3 = ell * ell * ell;
     ops->eps = eps;
+    ops->trunc = trunc;
     ops->homogeneous = is_homogeneous(kernel.type, &ops->hom_degree) ? 1 : 0;
     ops->ref_width = ops->homogeneous ? 1.0 : width;
     cudaGetDevice(&ops->device);

@@ -155,9 +155,10 @@ struct m2l_ops {
     m2l::Layout lrtc_tf32, lrtc_bf16x3, lrtc_tf32x3; // low-rank factor images of the tensor-core apply
     mutable m2l::Buckets ws;  // workspace of m2l_apply_level
     mutable double ws_scale = 1.0;  // scale of the level last classified into ws
+    int trunc = M2L_TRUNC_FROBENIUS;  // truncation criterion (m2l_truncation)
     int lowrank_method = 0;   // 0: truncated SVD, 1: ACA + truncated SVD
     int aca_terms[16] = {0};  // ACA terms before the recompression (method 1)
-    int jacobi_sweeps[16] = {0};
+    int jacobi_sweeps[16] = {0};  // sweeps of each operator's (method 0) or core's (method 1) SVD
     int *d_status = nullptr;  // device status word
     int debug_flags = 0;      // M2L_DEBUG_* test switches
 };
@@ -171,6 +172,17 @@ struct m2l_plan {
 };
 
 namespace m2l {
+
+// One-sided Jacobi SVD of nb column-major m x n matrices (m >= n), in place
+// (m2l_svd.cu): A <- A V with orthogonal columns, V [nb][n][n] (column-major,
+// may be null) the accumulated rotations, sigma [nb][n] the column norms
+// (unsorted), sweeps [nb] (host, may be null).  Synchronises the stream.
+m2l_status jacobi_svd(double *A, int m, int n, int nb, double *V, double *sigma, int *sweeps, cudaStream_t s);
+// order[0..n) = indices of sig by descending value (stable).
+void order_descending(const double *sig, int n, int *order);
+// Truncation rank of s (descending, length n) at accuracy eps under the
+// m2l_truncation criterion trunc; n for eps <= 0.
+int truncation_rank(const double *s, int n, double eps, int trunc);
 
 // Precompute (m2l_tables.cu)
 m2l_status build_tables(m2l_ops *ops, cudaStream_t s);

@@ -5,12 +5,12 @@
 // symmetry-blocked one, for comparison (the paper's Tables for SA/SArcmp).
 //
 // Set-up (synchronous): the 316 operators are expanded on the device from the
-// 16 unique ones (K_t[a][b] = K_p[sigma(a)][sigma(b)]); cuSOLVER gives the two
-// big SVDs; C_t = U^T (K_t B) by batched products; SArcmp by one small SVD per t.
+// 16 unique ones (K_t[a][b] = K_p[sigma(a)][sigma(b)]); one-sided Jacobi gives
+// the two big SVDs; C_t = U^T (K_t B) by batched products; SArcmp by one small
+// Jacobi SVD per t, all t in one batch.
 // Apply: compress every source, w^ = B^T w (one GEMM); per transfer vector t,
 // tiles of its interactions: gather w^, multiply by C_t (or by its two factors),
 // add into f^ of the targets; decompress, f += scale U f^ (one GEMM).
-#include <cusolverDn.h>
 #include <math.h>
 
 #include <algorithm>
@@ -113,15 +113,26 @@ __global__ void sa_expand_kernel(int n3, int nt, const int *__restrict__ slots, 
     }
 }
 
-// B [n3][r] and U^T [r][n3] from the right singular vectors (VT, column-major
-// n3 x n3) of K_col and of K_row^T.
-__global__ void sa_basis_kernel(int n3, int r, const double *__restrict__ vt_col, const double *__restrict__ vt_row,
+// B [n3][r] and U^T [r][n3] from the right singular vectors of K_col and of
+// K_row^T (Jacobi's V, column-major n3 x n3, vector ord[q] is the q-th largest).
+__global__ void sa_basis_kernel(int n3, int r, const int *__restrict__ ord_col, const double *__restrict__ v_col,
+                                const int *__restrict__ ord_row, const double *__restrict__ v_row,
                                 double *__restrict__ B, double *__restrict__ Ut)
 {
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n3 * r; idx += gridDim.x * blockDim.x) {
         const int j = idx / r, q = idx % r;
-        B[(size_t)j * r + q] = vt_col[q + (size_t)j * n3];
-        Ut[(size_t)q * n3 + j] = vt_row[q + (size_t)j * n3];
+        B[(size_t)j * r + q] = v_col[(size_t)ord_col[q] * n3 + j];
+        Ut[(size_t)q * n3 + j] = v_row[(size_t)ord_row[q] * n3 + j];
+    }
+}
+
+// Column-major copies of the row-major r x r cores, for their Jacobi SVDs.
+__global__ void sa_cores_colmajor_kernel(int r, int nt, const double *__restrict__ C, double *__restrict__ Ccm)
+{
+    const long rr = (long)r * r, total = (long)nt * rr;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const long t = i / rr, e = i % rr, col = e / r, row = e % r;
+        Ccm[i] = C[t * rr + row * r + col];
     }
 }
 
@@ -381,28 +392,25 @@ void sa_release(m2l_sa *a)
 
 // Scratch of the set-up, released on every return.
 struct SaScratch {
-    DevBuf dslots, Krm, Kcol, KrowT, S1, S2, VT1, VT2, work, info, T1, Cfull, cS, cU, cVT, ctmp;
-    cusolverDnHandle_t h = nullptr;
+    DevBuf dslots, Krm, Kcol, KrowT, S1, S2, V1, V2, ord1, ord2, T1, Cfull, Ccm, Vc, sc;
     ~SaScratch()
     {
         cudaDeviceSynchronize();
-        DevBuf *bs[] = {&dslots, &Krm, &Kcol, &KrowT, &S1, &S2, &VT1, &VT2, &work, &info, &T1, &Cfull,
-                        &cS, &cU, &cVT, &ctmp};
+        DevBuf *bs[] = {&dslots, &Krm, &Kcol, &KrowT, &S1, &S2, &V1, &V2, &ord1, &ord2, &T1, &Cfull, &Ccm, &Vc, &sc};
         for (DevBuf *b : bs) b->release();
-        if (h) cusolverDnDestroy(h);
     }
 };
 
 #define SA_TRY(x) do { m2l_status st_ = (x); if (st_ != M2L_OK) return st_; } while (0)
-#define SA_SOLVER(x, what) do { if ((x) != CUSOLVER_STATUS_SUCCESS) { set_error("cuSOLVER: %s failed", what); return M2L_ECUDA; } } while (0)
 
-// Truncation rank at relative accuracy eps: the number of singular values above
-// eps times the largest (all of them for eps = 0).
-int sa_rank(const std::vector<double> &sv, int n, double eps)
+// Order (descending) and truncation rank of one set of Jacobi singular values.
+int sa_rank(const std::vector<double> &sv, int n, double eps, int trunc, std::vector<int> &order)
 {
-    if (eps <= 0.0) return n;
-    int r = 0;
-    while (r < n && sv[r] > eps * sv[0]) ++r;
+    order.resize(n);
+    order_descending(sv.data(), n, order.data());
+    std::vector<double> sorted(n);
+    for (int i = 0; i < n; ++i) sorted[i] = sv[order[i]];
+    const int r = truncation_rank(sorted.data(), n, eps, trunc);
     return r < 1 ? 1 : r;
 }
 
@@ -426,9 +434,10 @@ m2l_status sa_build(m2l_sa *a, cudaStream_t s)
     SA_TRY(w.KrowT.ensure((size_t)m * n3 * sizeof(double)));
     SA_TRY(w.S1.ensure(n3 * sizeof(double)));
     SA_TRY(w.S2.ensure(n3 * sizeof(double)));
-    SA_TRY(w.VT1.ensure((size_t)n3 * n3 * sizeof(double)));
-    SA_TRY(w.VT2.ensure((size_t)n3 * n3 * sizeof(double)));
-    SA_TRY(w.info.ensure(2 * sizeof(int)));
+    SA_TRY(w.V1.ensure((size_t)n3 * n3 * sizeof(double)));
+    SA_TRY(w.V2.ensure((size_t)n3 * n3 * sizeof(double)));
+    SA_TRY(w.ord1.ensure(n3 * sizeof(int)));
+    SA_TRY(w.ord2.ensure(n3 * sizeof(int)));
     M2L_CUDA(cudaMemcpy(w.dslots.p, slots.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
     sa_expand_kernel<<<sa_grid((long)m * n3), 256, 0, s>>>(n3, nt, w.dslots.as<int>(), ops->lut.as<uint16_t>(),
                                                              ops->sigma.as<int16_t>(), ops->K64.as<double>(),
@@ -436,25 +445,16 @@ m2l_status sa_build(m2l_sa *a, cudaStream_t s)
                                                              w.KrowT.as<double>());
     M2L_LAUNCH_CHECK("sa_expand_kernel");
     M2L_CUDA(cudaStreamSynchronize(s));
-    // the two SVDs of Eq. (17); only the right singular vectors are formed
-    SA_SOLVER(cusolverDnCreate(&w.h), "create");
-    SA_SOLVER(cusolverDnSetStream(w.h, s), "set stream");
-    int lwork = 0;
-    SA_SOLVER(cusolverDnDgesvd_bufferSize(w.h, (int)m, n3, &lwork), "gesvd buffer size");
-    SA_TRY(w.work.ensure((size_t)lwork * sizeof(double)));
-    SA_SOLVER(cusolverDnDgesvd(w.h, 'N', 'A', (int)m, n3, w.Kcol.as<double>(), (int)m, w.S1.as<double>(), nullptr, 1,
-                               w.VT1.as<double>(), n3, w.work.as<double>(), lwork, nullptr, w.info.as<int>()),
-              "gesvd of K_col");
-    SA_SOLVER(cusolverDnDgesvd(w.h, 'N', 'A', (int)m, n3, w.KrowT.as<double>(), (int)m, w.S2.as<double>(), nullptr,
-                               1, w.VT2.as<double>(), n3, w.work.as<double>(), lwork, nullptr, w.info.as<int>() + 1),
-              "gesvd of K_row^T");
+    // the two SVDs of Eq. (17) by one-sided Jacobi; only the right singular
+    // vectors (the accumulated rotations) are kept
+    SA_TRY(jacobi_svd(w.Kcol.as<double>(), (int)m, n3, 1, w.V1.as<double>(), w.S1.as<double>(), nullptr, s));
+    SA_TRY(jacobi_svd(w.KrowT.as<double>(), (int)m, n3, 1, w.V2.as<double>(), w.S2.as<double>(), nullptr, s));
     std::vector<double> s1(n3), s2(n3);
-    int hinfo[2];
+    std::vector<int> o1, o2;
     M2L_CUDA(cudaMemcpy(s1.data(), w.S1.p, n3 * sizeof(double), cudaMemcpyDeviceToHost));
     M2L_CUDA(cudaMemcpy(s2.data(), w.S2.p, n3 * sizeof(double), cudaMemcpyDeviceToHost));
-    M2L_CUDA(cudaMemcpy(hinfo, w.info.p, 2 * sizeof(int), cudaMemcpyDeviceToHost));
-    if (hinfo[0] != 0 || hinfo[1] != 0) { set_error("gesvd of the joined operators did not converge"); return M2L_ECUDA; }
-    const int r = std::max(sa_rank(s2, n3, a->eps), sa_rank(s1, n3, a->eps));
+    const int trunc = a->ops->trunc;
+    const int r = std::max(sa_rank(s2, n3, a->eps, trunc, o2), sa_rank(s1, n3, a->eps, trunc, o1));
     if (r > kSaMaxRank) {
         set_error("SA rank %d exceeds %d", r, kSaMaxRank);
         return M2L_EUNSUPPORTED;
@@ -462,7 +462,10 @@ m2l_status sa_build(m2l_sa *a, cudaStream_t s)
     a->r = r;
     SA_TRY(a->B64.ensure((size_t)n3 * r * sizeof(double)));
     SA_TRY(a->U64t.ensure((size_t)r * n3 * sizeof(double)));
-    sa_basis_kernel<<<sa_grid((long)n3 * r), 256, 0, s>>>(n3, r, w.VT1.as<double>(), w.VT2.as<double>(),
+    M2L_CUDA(cudaMemcpy(w.ord1.p, o1.data(), n3 * sizeof(int), cudaMemcpyHostToDevice));
+    M2L_CUDA(cudaMemcpy(w.ord2.p, o2.data(), n3 * sizeof(int), cudaMemcpyHostToDevice));
+    sa_basis_kernel<<<sa_grid((long)n3 * r), 256, 0, s>>>(n3, r, w.ord1.as<int>(), w.V1.as<double>(),
+                                                          w.ord2.as<int>(), w.V2.as<double>(),
                                                           a->B64.as<double>(), a->U64t.as<double>());
     M2L_LAUNCH_CHECK("sa_basis_kernel");
     // C_t = U^T (K_t B), Eq. (18), for the 316 transfer vectors
@@ -481,16 +484,27 @@ m2l_status sa_build(m2l_sa *a, cudaStream_t s)
     M2L_CUDA(cudaMemsetAsync(a->X64.p, 0, 343 * rr * sizeof(double), s));
     M2L_CUDA(cudaMemsetAsync(a->Y64.p, 0, 343 * rr * sizeof(double), s));
     a->kt.assign(343, 0);
-    int clwork = 0;
+    // SArcmp, Eq. (19): one-sided Jacobi SVD of every core, C_t V = W Sigma, so
+    // C_t ~ X_t Y_t^T with X_t = (W Sigma)_k (column-major Jacobi output) and
+    // Y_t = V_k, the k = r_t largest; kept only when 2 r_t < r.
+    std::vector<double> hW, hV, hs;
+    std::vector<int> ord;
     if (a->recompress) {
-        SA_TRY(w.cS.ensure(r * sizeof(double)));
-        SA_TRY(w.cU.ensure(rr * sizeof(double)));
-        SA_TRY(w.cVT.ensure(rr * sizeof(double)));
-        SA_TRY(w.ctmp.ensure(rr * sizeof(double)));
-        SA_SOLVER(cusolverDnDgesvd_bufferSize(w.h, r, r, &clwork), "gesvd buffer size");
-        SA_TRY(w.work.ensure((size_t)clwork * sizeof(double)));
+        SA_TRY(w.Ccm.ensure((size_t)nt * rr * sizeof(double)));
+        SA_TRY(w.Vc.ensure((size_t)nt * rr * sizeof(double)));
+        SA_TRY(w.sc.ensure((size_t)nt * r * sizeof(double)));
+        sa_cores_colmajor_kernel<<<sa_grid((long)nt * rr), 256, 0, s>>>(r, nt, w.Cfull.as<double>(),
+                                                                        w.Ccm.as<double>());
+        M2L_LAUNCH_CHECK("sa_cores_colmajor_kernel");
+        SA_TRY(jacobi_svd(w.Ccm.as<double>(), r, r, nt, w.Vc.as<double>(), w.sc.as<double>(), nullptr, s));
+        hW.resize((size_t)nt * rr);
+        hV.resize((size_t)nt * rr);
+        hs.resize((size_t)nt * r);
+        M2L_CUDA(cudaMemcpy(hW.data(), w.Ccm.p, hW.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        M2L_CUDA(cudaMemcpy(hV.data(), w.Vc.p, hV.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        M2L_CUDA(cudaMemcpy(hs.data(), w.sc.p, hs.size() * sizeof(double), cudaMemcpyDeviceToHost));
     }
-    std::vector<double> cs(r), cu(rr), cvt(rr), hX(rr), hY(rr);
+    std::vector<double> cs(r), hX(rr), hY(rr);
     for (int i = 0; i < nt; ++i) {
         const int sl = slots[i];
         double *Cd = w.Cfull.as<double>() + (size_t)i * rr;
@@ -498,28 +512,20 @@ m2l_status sa_build(m2l_sa *a, cudaStream_t s)
         double *Yd = a->Y64.as<double>() + (size_t)sl * rr;
         int k = 0;
         if (a->recompress) {
-            // SArcmp, Eq. (19).  Read column-major, the row-major C_t is C_t^T = U' S V'^T,
-            // so C_t = V' S U'^T ~ (V'_k S_k) U'_k^T: X_t = V'_k S_k, Y_t = U'_k.
-            M2L_CUDA(cudaMemcpyAsync(w.ctmp.p, Cd, rr * sizeof(double), cudaMemcpyDeviceToDevice, s));
-            SA_SOLVER(cusolverDnDgesvd(w.h, 'A', 'A', r, r, w.ctmp.as<double>(), r, w.cS.as<double>(),
-                                       w.cU.as<double>(), r, w.cVT.as<double>(), r, w.work.as<double>(), clwork,
-                                       nullptr, w.info.as<int>()),
-                      "gesvd of C_t");
-            M2L_CUDA(cudaMemcpy(hinfo, w.info.p, sizeof(int), cudaMemcpyDeviceToHost));
-            if (hinfo[0] != 0) { set_error("gesvd of C_t did not converge"); return M2L_ECUDA; }
-            M2L_CUDA(cudaMemcpy(cs.data(), w.cS.p, r * sizeof(double), cudaMemcpyDeviceToHost));
-            M2L_CUDA(cudaMemcpy(cu.data(), w.cU.p, rr * sizeof(double), cudaMemcpyDeviceToHost));
-            M2L_CUDA(cudaMemcpy(cvt.data(), w.cVT.p, rr * sizeof(double), cudaMemcpyDeviceToHost));
-            const int rt = sa_rank(cs, r, a->eps);
+            std::copy(hs.begin() + (size_t)i * r, hs.begin() + (size_t)(i + 1) * r, cs.begin());
+            const int rt = sa_rank(cs, r, a->eps, trunc, ord);
             if (2 * rt < r) {
                 k = rt;
+                const double *Wt = hW.data() + (size_t)i * rr, *Vt = hV.data() + (size_t)i * rr;
                 std::fill(hX.begin(), hX.end(), 0.0);
                 std::fill(hY.begin(), hY.end(), 0.0);
-                for (int row = 0; row < r; ++row)
-                    for (int q = 0; q < k; ++q) {
-                        hX[(size_t)row * r + q] = cvt[q + (size_t)row * r] * cs[q];   // V'(row, q) s_q
-                        hY[(size_t)row * r + q] = cu[row + (size_t)q * r];            // U'(row, q)
+                for (int q = 0; q < k; ++q) {
+                    const size_t col = (size_t)ord[q] * r;
+                    for (int row = 0; row < r; ++row) {
+                        hX[(size_t)row * r + q] = Wt[col + row];   // (W Sigma)(row, q-th)
+                        hY[(size_t)row * r + q] = Vt[col + row];   // V(row, q-th)
                     }
+                }
                 M2L_CUDA(cudaMemcpy(Xd, hX.data(), rr * sizeof(double), cudaMemcpyHostToDevice));
                 M2L_CUDA(cudaMemcpy(Yd, hY.data(), rr * sizeof(double), cudaMemcpyHostToDevice));
                 a->n_recompressed++;

@@ -9,8 +9,7 @@
 //  * sigma_g(j) = m(pi(m^{-1}(j))), pi = pi^D o pi^A (Eqs. (26)-(29)), one
 //    table per signed axis permutation g = 8 * perm_id + flip_mask.
 //  * t -> (p(t), g(t)) for the 343 vectors of [-3, 3]^3.
-#include <cusolverDn.h>
-
+#include <algorithm>
 #include <vector>
 
 #include "m2l_internal.cuh"
@@ -114,10 +113,22 @@ __global__ void assemble_kernel(int ell, int kind, double c, double w, const int
 
 // U_p = U_K Sigma (first r_p columns), V_p = V_K, both [n3][rmax] row-major,
 // from the column-major SVD M = U_M S V_M^T of M = K_p^T (so U_K = V_M, V_K = U_M).
-__global__ void extract_lowrank_kernel(int n3, int rmax, const int *__restrict__ ranks,
-                                       const double *__restrict__ S, const double *__restrict__ UM,
-                                       const double *__restrict__ VTM, double *__restrict__ U,
-                                       double *__restrict__ V)
+// A[p] = K_p^T stored row-major, i.e. K_p column-major: column j of K_p contiguous.
+__global__ void to_column_major_kernel(int n3, const double *__restrict__ K, double *__restrict__ A)
+{
+    const long nn = (long)n3 * n3, total = 16 * nn;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const long p = i / nn, r = i % nn, col = r / n3, row = r % n3;
+        A[i] = K[p * nn + row * n3 + col];
+    }
+}
+
+// After the one-sided Jacobi SVD K_p V = W Sigma (A holds W Sigma column-major):
+// U[p][row][q] = (W Sigma)(row, order_q), V[p][row][q] = V(row, order_q) for
+// q < r_p, zero beyond (the [16][n3][rmax] layout of the factors).
+__global__ void extract_lowrank_kernel(int n3, int rmax, const int *__restrict__ ranks, const int *__restrict__ order,
+                                       const double *__restrict__ A, const double *__restrict__ Vr,
+                                       double *__restrict__ U, double *__restrict__ V)
 {
     const int p = blockIdx.y;
     const int r = ranks[p];
@@ -126,8 +137,9 @@ __global__ void extract_lowrank_kernel(int n3, int rmax, const int *__restrict__
         const int row = idx / rmax, k = idx % rmax;
         double u = 0.0, v = 0.0;
         if (k < r) {
-            u = VTM[p * nn + k + (long)row * n3] * S[p * n3 + k];   // VT_M (k, row)
-            v = UM[p * nn + row + (long)k * n3];                    // U_M (row, k)
+            const long col = order[p * n3 + k];
+            u = A[p * nn + col * n3 + row];
+            v = Vr[p * nn + col * n3 + row];
         }
         U[(long)p * n3 * rmax + idx] = u;
         V[(long)p * n3 * rmax + idx] = v;
@@ -196,58 +208,34 @@ m2l_status assemble_operators(m2l_ops *ops, cudaStream_t s)
     return M2L_OK;
 }
 
+// Step a1's truncated SVD of the 16 operators (Eq. (20)), by one-sided Jacobi
+// on the device; ranks by the ops' truncation criterion.
 m2l_status lowrank_factors(m2l_ops *ops)
 {
     const int n = ops->n3;
     const size_t nn = (size_t)n * n;
-    DevBuf A, S, UM, VTM, work, info, dranks;
-    ScratchGuard guard{&A, &S, &UM, &VTM, &work, &info, &dranks};
+    DevBuf A, S, VR, dord, dranks;
+    ScratchGuard guard{&A, &S, &VR, &dord, &dranks};
     m2l_status st;
     if ((st = A.ensure(16 * nn * sizeof(double))) != M2L_OK) return st;
     if ((st = S.ensure(16 * (size_t)n * sizeof(double))) != M2L_OK) return st;
-    if ((st = UM.ensure(16 * nn * sizeof(double))) != M2L_OK) return st;
-    if ((st = VTM.ensure(16 * nn * sizeof(double))) != M2L_OK) return st;
-    if ((st = info.ensure(16 * sizeof(int))) != M2L_OK) return st;
-    // gesvd overwrites its input: work on a copy of the operators
-    M2L_CUDA(cudaMemcpy(A.p, ops->K64.p, 16 * nn * sizeof(double), cudaMemcpyDeviceToDevice));
-    cusolverDnHandle_t h = nullptr;
-    if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS) {
-        set_error("cusolverDnCreate failed");
-        return M2L_ECUDA;
-    }
-    int lwork = 0;
-    m2l_status result = M2L_OK;
-    if (cusolverDnDgesvd_bufferSize(h, n, n, &lwork) != CUSOLVER_STATUS_SUCCESS) {
-        set_error("cusolverDnDgesvd_bufferSize failed");
-        result = M2L_ECUDA;
-    }
-    if (result == M2L_OK) result = work.ensure((size_t)lwork * sizeof(double));
-    for (int p = 0; p < 16 && result == M2L_OK; ++p) {
-        // column-major view of the row-major K_p is M = K_p^T
-        cusolverStatus_t cs = cusolverDnDgesvd(
-            h, 'A', 'A', n, n, A.as<double>() + p * nn, n, S.as<double>() + (size_t)p * n,
-            UM.as<double>() + p * nn, n, VTM.as<double>() + p * nn, n, work.as<double>(), lwork, nullptr,
-            info.as<int>() + p);
-        if (cs != CUSOLVER_STATUS_SUCCESS) {
-            set_error("cusolverDnDgesvd failed for operator %d (status %d)", p, (int)cs);
-            result = M2L_ECUDA;
-        }
-    }
-    cusolverDnDestroy(h);
-    if (result != M2L_OK) return result;
-    std::vector<double> hS(16 * (size_t)n);
-    std::vector<int> hinfo(16);
+    if ((st = VR.ensure(16 * nn * sizeof(double))) != M2L_OK) return st;
+    if ((st = dord.ensure(16 * (size_t)n * sizeof(int))) != M2L_OK) return st;
+    if ((st = dranks.ensure(16 * sizeof(int))) != M2L_OK) return st;
+    to_column_major_kernel<<<(int)std::min<size_t>((16 * nn + 255) / 256, 65535), 256>>>(n, ops->K64.as<double>(),
+                                                                                         A.as<double>());
+    M2L_LAUNCH_CHECK("to_column_major_kernel");
+    if ((st = jacobi_svd(A.as<double>(), n, n, 16, VR.as<double>(), S.as<double>(), ops->jacobi_sweeps, 0)) != M2L_OK)
+        return st;
+    std::vector<double> hS(16 * (size_t)n), sorted(n);
+    std::vector<int> hord(16 * (size_t)n);
     M2L_CUDA(cudaMemcpy(hS.data(), S.p, hS.size() * sizeof(double), cudaMemcpyDeviceToHost));
-    M2L_CUDA(cudaMemcpy(hinfo.data(), info.p, 16 * sizeof(int), cudaMemcpyDeviceToHost));
     int rmax = 1;
     for (int p = 0; p < 16; ++p) {
-        if (hinfo[p] != 0) {
-            set_error("gesvd did not converge for operator %d (info %d)", p, hinfo[p]);
-            return M2L_ECUDA;
-        }
-        const double *s = hS.data() + (size_t)p * n;
-        int r = 0;
-        while (r < n && s[r] > ops->eps * s[0]) ++r;   // smallest r with s_{r+1} <= eps s_1
+        int *o = hord.data() + (size_t)p * n;
+        order_descending(hS.data() + (size_t)p * n, n, o);
+        for (int i = 0; i < n; ++i) sorted[i] = hS[(size_t)p * n + o[i]];
+        int r = truncation_rank(sorted.data(), n, ops->eps, ops->trunc);
         if (r < 1) r = 1;
         ops->ranks[p] = r;
         if (r > rmax) rmax = r;
@@ -255,11 +243,11 @@ m2l_status lowrank_factors(m2l_ops *ops)
     ops->rmax = rmax;
     if ((st = ops->U64.ensure(16 * (size_t)n * rmax * sizeof(double))) != M2L_OK) return st;
     if ((st = ops->V64.ensure(16 * (size_t)n * rmax * sizeof(double))) != M2L_OK) return st;
-    if ((st = dranks.ensure(16 * sizeof(int))) != M2L_OK) return st;
     M2L_CUDA(cudaMemcpy(dranks.p, ops->ranks, 16 * sizeof(int), cudaMemcpyHostToDevice));
+    M2L_CUDA(cudaMemcpy(dord.p, hord.data(), hord.size() * sizeof(int), cudaMemcpyHostToDevice));
     dim3 grid((n * rmax + 255) / 256, 16);
-    extract_lowrank_kernel<<<grid, 256>>>(n, rmax, dranks.as<int>(), S.as<double>(), UM.as<double>(),
-                                          VTM.as<double>(), ops->U64.as<double>(), ops->V64.as<double>());
+    extract_lowrank_kernel<<<grid, 256>>>(n, rmax, dranks.as<int>(), dord.as<int>(), A.as<double>(), VR.as<double>(),
+                                          ops->U64.as<double>(), ops->V64.as<double>());
     M2L_LAUNCH_CHECK("extract_lowrank_kernel");
     M2L_CUDA(cudaDeviceSynchronize());
     return M2L_OK;

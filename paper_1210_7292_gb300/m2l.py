@@ -94,6 +94,9 @@ def lib():
             "m2l_sa_apply_level": [P, ctypes.POINTER(m2l_level), P, P, I, I, P],
             "m2l_precompute_aca": [m2l_kernel, I, D, D, ctypes.POINTER(P)],
             "m2l_ops_aca_info": [P, P, P],
+            "m2l_precompute_ex": [m2l_kernel, I, D, D, I, I, ctypes.POINTER(P)],
+            "m2l_ops_truncation": [P, ctypes.POINTER(I)],
+            "m2l_ops_svd_sweeps": [P, P],
             "m2l_dfmm_build_lists": [I, D, D, I, P, I, P, P, P, P, P, P],
             "m2l_dfmm_plan_create": [I, D, ctypes.POINTER(m2l_dlevel), P, ctypes.POINTER(P)],
             "m2l_dfmm_plan_info": [P, P, P, P, P, P],
@@ -203,19 +206,47 @@ class Level:
         return int(self.struct.nnz)
 
 
-def m2l_precompute(kernel_type, ell, eps=0.0, width=0.0, c=0.0) -> Ops:
+M2L_TRUNC_FROBENIUS, M2L_TRUNC_SPECTRAL = 0, 1
+_TRUNC = {"frobenius": M2L_TRUNC_FROBENIUS, "spectral": M2L_TRUNC_SPECTRAL}
+
+
+def _trunc_code(truncation):
+    if isinstance(truncation, str):
+        if truncation not in _TRUNC:
+            raise ValueError("truncation must be one of %s, got %r" % (sorted(_TRUNC), truncation))
+        return _TRUNC[truncation]
+    return int(truncation)
+
+
+def m2l_precompute(kernel_type, ell, eps=0.0, width=0.0, c=0.0, truncation="frobenius") -> Ops:
+    """Operators and tables; low-rank factors at accuracy eps under the
+    truncation criterion ("frobenius" or "spectral") when eps > 0."""
     h = ctypes.c_void_p()
-    _check("m2l_precompute", lib().m2l_precompute(m2l_kernel(int(kernel_type), float(c)), int(ell), float(eps),
-                                                  float(width), ctypes.byref(h)))
+    _check("m2l_precompute_ex", lib().m2l_precompute_ex(m2l_kernel(int(kernel_type), float(c)), int(ell), float(eps),
+                                                        float(width), _trunc_code(truncation), 0, ctypes.byref(h)))
     return Ops(h, int(ell))
 
 
-def m2l_precompute_aca(kernel_type, ell, eps=0.0, width=0.0, c=0.0) -> Ops:
+def m2l_precompute_aca(kernel_type, ell, eps=0.0, width=0.0, c=0.0, truncation="frobenius") -> Ops:
     """m2l_precompute with the low-rank factors from ACA + truncated SVD."""
     h = ctypes.c_void_p()
-    _check("m2l_precompute_aca", lib().m2l_precompute_aca(m2l_kernel(int(kernel_type), float(c)), int(ell),
-                                                          float(eps), float(width), ctypes.byref(h)))
+    _check("m2l_precompute_ex", lib().m2l_precompute_ex(m2l_kernel(int(kernel_type), float(c)), int(ell), float(eps),
+                                                        float(width), _trunc_code(truncation), 1, ctypes.byref(h)))
     return Ops(h, int(ell))
+
+
+def m2l_ops_truncation(ops: Ops) -> str:
+    """The truncation criterion ops were built with ("frobenius" or "spectral")."""
+    v = ctypes.c_int()
+    _check("m2l_ops_truncation", lib().m2l_ops_truncation(ops.handle, ctypes.byref(v)))
+    return {c: n for n, c in _TRUNC.items()}[v.value]
+
+
+def m2l_ops_svd_sweeps(ops: Ops):
+    """Jacobi sweeps [16] of the SVD of each operator (or ACA core)."""
+    sweeps = np.zeros(16, dtype=np.int32)
+    _check("m2l_ops_svd_sweeps", lib().m2l_ops_svd_sweeps(ops.handle, sweeps.ctypes.data))
+    return sweeps
 
 
 def m2l_ops_aca_info(ops: Ops):

@@ -21,16 +21,16 @@ def make_level(m2l, cells_np, level):
     return m2l.Level(oracle.cell_width(level), ijk, ijk, off, src, level)
 
 
-def oracle_ops(ell, kind, level, eps=0.0):
+def oracle_ops(ell, kind, level, eps=0.0, truncation=oracle.FROBENIUS):
     ops = oracle.operator_table(ell, kind, KIND_C[kind], level)
     if eps > 0:
-        ops, _ = oracle.lowrank_operator_table(ops, eps)
+        ops, _ = oracle.lowrank_operator_table(ops, eps, truncation)
     return ops
 
 
-def gpu_ops(m2l, ell, kind, level, eps=0.0):
+def gpu_ops(m2l, ell, kind, level, eps=0.0, truncation="frobenius"):
     width = oracle.cell_width(level)
-    return m2l.m2l_precompute(kind, ell, eps, width if kind == 2 else 0.0, KIND_C[kind])
+    return m2l.m2l_precompute(kind, ell, eps, width if kind == 2 else 0.0, KIND_C[kind], truncation=truncation)
 
 
 def pruned_cells(level, keep, seed):

@@ -23,37 +23,42 @@ def m2l():
     return mod
 
 
-def _ops(m2l, fn, ell, kind, eps, level):
+def _ops(m2l, fn, ell, kind, eps, level, trunc="frobenius"):
     w = oracle.cell_width(level)
-    return fn(kind, ell, eps, w if kind == 2 else 0.0, KIND_C[kind])
+    return fn(kind, ell, eps, w if kind == 2 else 0.0, KIND_C[kind], truncation=trunc)
 
 
+@pytest.mark.parametrize("trunc", ["frobenius", "spectral"])
 @pytest.mark.parametrize("ell,kind,eps", [(3, 0, 1e-3), (5, 0, 1e-5), (5, 1, 1e-6), (6, 2, 1e-6), (7, 1, 1e-7),
                                           (8, 0, 1e-8)])
-def test_aca_ranks_and_bound(m2l, ell, kind, eps):
+def test_aca_ranks_and_bound(m2l, ell, kind, eps, trunc):
     level = 3
-    ops_a = _ops(m2l, m2l.m2l_precompute_aca, ell, kind, eps, level)
-    ops_s = _ops(m2l, m2l.m2l_precompute, ell, kind, eps, level)
+    ops_a = _ops(m2l, m2l.m2l_precompute_aca, ell, kind, eps, level, trunc)
+    ops_s = _ops(m2l, m2l.m2l_precompute, ell, kind, eps, level, trunc)
     ranks_a = m2l.m2l_ops_query(ops_a)[0]
     ranks_s = m2l.m2l_ops_query(ops_s)[0]
     terms, sweeps = m2l.m2l_ops_aca_info(ops_a)
     K = m2l.m2l_ops_copy_operators(ops_a)
-    ref_ranks = []
+    ref_ranks, ref_ranks_a = [], []
     worst = 0.0
     for p, t in enumerate(oracle.t_sym_list()):
         Kp = oracle.operator_for_t(ell, kind, KIND_C[kind], level, t)
-        _, _, r = oracle.lowrank(Kp, eps)
-        _, _, ra, _ = oracle.aca_lowrank(Kp, eps)
-        assert ra == r
+        _, _, r = oracle.lowrank(Kp, eps, trunc)
+        _, _, ra, _ = oracle.aca_lowrank(Kp, eps, trunc)
+        sk = np.linalg.svd(Kp, compute_uv=False)
+        # equal ranks, but for a cut the SVD moved past a cluster of equal values
+        assert ra == r or (ra < r and sk[ra - 1] - sk[r - 1] <= oracle.CLUSTER_GAP * sk[0])
         ref_ranks.append(r)
+        ref_ranks_a.append(ra)
         U, V = m2l.m2l_ops_copy_lowrank(ops_a, p)
-        s1 = np.linalg.norm(K[p], 2)
-        worst = max(worst, np.linalg.norm(K[p] - U @ V.T, 2) / s1)
-    print("ell=%d kind=%d eps=%g: ranks %s, ACA terms %d-%d, Jacobi sweeps <= %d, max |K - UV^T|_2 / s1 = %.2e"
-          % (ell, kind, eps, list(ranks_a), terms.min(), terms.max(), sweeps.max(), worst))
-    assert list(ranks_a) == list(ranks_s) == ref_ranks
+        nrm = 2 if trunc == "spectral" else "fro"
+        worst = max(worst, np.linalg.norm(K[p] - U @ V.T, nrm) / np.linalg.norm(K[p], nrm))
+    print("ell=%d kind=%d eps=%g %s: ranks %s, ACA terms %d-%d, Jacobi sweeps <= %d, max |K - UV^T| / |K| = %.2e"
+          % (ell, kind, eps, trunc, list(ranks_a), terms.min(), terms.max(), sweeps.max(), worst))
+    assert list(ranks_a) == ref_ranks_a and list(ranks_s) == ref_ranks
     assert np.all(terms >= ranks_a) and sweeps.max() < 60
-    assert worst <= 1.01 * eps
+    # truncation bound of the approximant plus the ACA residual (below eps |K|)
+    assert worst <= (1.01 if trunc == "spectral" else 2.0) * eps
 
 
 @pytest.mark.parametrize("ell,kind,eps", [(5, 0, 1e-5), (7, 1, 1e-7)])

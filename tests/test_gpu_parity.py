@@ -266,27 +266,38 @@ def test_adjoint_matches_oracle_transpose(m2l, prec):
 
 
 # ---------------------------------------------------------------- low rank
+@pytest.mark.parametrize("trunc", ["frobenius", "spectral"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("ell,kind,eps", [(5, 0, 1e-5), (7, 1, 1e-7)])
-def test_lowrank_matches_oracle(m2l, prec, ell, kind, eps):
+def test_lowrank_matches_oracle(m2l, prec, ell, kind, eps, trunc):
+    """Step a1 by the device's one-sided Jacobi SVD: the ranks under either
+    truncation criterion equal the oracle's (LAPACK SVD), the truncated
+    operators agree to 1e-12 s_1, and the apply matches the oracle's."""
     level = 3
     cells = pruned_cells(level, 0.4, 21)
     w = np.random.default_rng(4).standard_normal((len(cells), ell ** 3))
     lv = make_level(m2l, cells, level)
-    ops = gpu_ops(m2l, ell, kind, level, eps=eps)
+    ops = gpu_ops(m2l, ell, kind, level, eps=eps, truncation=trunc)
+    assert m2l.m2l_ops_truncation(ops) == trunc
+    sweeps = m2l.m2l_ops_svd_sweeps(ops)
+    assert 0 < sweeps.min() and sweeps.max() < 100
     ranks, _, _ = m2l.m2l_ops_query(ops)
     tsym = oracle.t_sym_list()
     full = oracle.operator_table(ell, kind, KIND_C[kind], level)
     for p, t in enumerate(tsym):
         s = np.linalg.svd(full[oracle.t_slot(t)], compute_uv=False)
-        assert ranks[p] == oracle.truncation_rank(s, eps)
+        assert ranks[p] == oracle.truncation_rank(s, eps, trunc)
         U, V = m2l.m2l_ops_copy_lowrank(ops, p)
         info = m2l.m2l_ops_info(ops)
         sc = (oracle.cell_width(level) / info["ref_width"]) ** info["homogeneity_degree"]
-        Ko, Vo, r = oracle.lowrank(full[oracle.t_slot(t)], eps)
+        Ko, Vo, r = oracle.lowrank(full[oracle.t_slot(t)], eps, trunc)
         assert np.allclose(sc * U @ V.T, Ko @ Vo.T, rtol=0, atol=1e-12 * s[0])
+        # the device's factor columns are orthogonal: V orthonormal, U = U_K Sigma
+        assert np.abs(V.T @ V - np.eye(r)).max() < 1e-12
+        G = U.T @ U
+        assert np.abs(G - np.diag(np.diag(G))).max() < 1e-12 * G[0, 0]
     off, src = oracle.interaction_lists(cells, cells)
-    ops_lr, _ = oracle.lowrank_operator_table(full, eps)
+    ops_lr, _ = oracle.lowrank_operator_table(full, eps, trunc)
     ref = oracle.m2l_apply(ops_lr, cells, cells, off, src, w)
     _compare(_run_apply(m2l, ops, lv, w, prec), ref, TOL[prec])
 

@@ -34,13 +34,17 @@ CASES = [(4, 0, 1e-4, False), (5, 0, 1e-5, False), (5, 0, 1e-5, True), (5, 1, 1e
          (3, 0, 1e-3, True), (3, 0, 0.0, False)]
 
 
+@pytest.mark.parametrize("trunc", ["frobenius", "spectral"])
 @pytest.mark.parametrize("ell,kind,eps,rcmp", CASES)
-def test_sa_factors_match_oracle(m2l, ell, kind, eps, rcmp):
+def test_sa_factors_match_oracle(m2l, ell, kind, eps, rcmp, trunc):
+    """The device's Jacobi SVDs of K_col, K_row^T and of every core give the
+    oracle's (LAPACK's) ranks under either truncation criterion."""
     level = 3
-    ops = gpu_ops(m2l, ell, kind, level)
+    ops = gpu_ops(m2l, ell, kind, level, truncation=trunc)
     sa = m2l.m2l_sa_create(ops, eps, rcmp)
     r, nrc, rt = m2l.m2l_sa_info(sa)
-    table, sa_ref, ranks = oracle.sa_operator_table(oracle.operator_table(ell, kind, KIND_C[kind], level), eps, rcmp)
+    table, sa_ref, ranks = oracle.sa_operator_table(oracle.operator_table(ell, kind, KIND_C[kind], level), eps, rcmp,
+                                                    trunc)
     assert r == sa_ref["r"]
     if rcmp:
         expect = np.where((ranks > 0) & (ranks < r), ranks, 0)
