@@ -586,8 +586,9 @@ m2l_status launch_big(const m2l_ops *ops, const Buckets &b, Layout &L, const flo
                       double scale, cudaStream_t s)
 {
     using Tr = TcTraits<KIND>;
-    constexpr int EG = real_eg<KIND, MT, KA>();
-    using C = BigCfg<KIND, MT, KA, kBigNT, EG>;
+    constexpr int NT = big_nt<KIND, MT, KA>();
+    constexpr int EG = big_eg<KIND, MT, KA>();
+    using C = BigCfg<KIND, MT, KA, NT, EG>;
     const int n3 = ops->n3;
     const size_t img_bytes = (size_t)16 * MT * KA * C::A_BLOCK;
     m2l_status st;
@@ -609,10 +610,10 @@ m2l_status launch_big(const m2l_ops *ops, const Buckets &b, Layout &L, const flo
         set_error("tensor-core kernel for ell = %d needs %d bytes of shared memory", ops->ell, C::SMEM);
         return M2L_EUNSUPPORTED;
     }
-    auto kern = tc_big_kernel<KIND, MT, KA, kBigNT, EG>;
+    auto kern = tc_big_kernel<KIND, MT, KA, NT, EG>;
     M2L_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
     long grid = num_sms();
-    const long tiles_bound = (long)(b.nnz + kBigNT - 1) / kBigNT + 16;
+    const long tiles_bound = (long)(b.nnz + NT - 1) / NT + 16;
     if (grid > tiles_bound) grid = tiles_bound;
     kern<<<(int)grid, big_threads(EG), C::SMEM, s>>>(b.rec.as<int2>(), b.class_off.as<int>(), L.a.as<uint8_t>(),
                                                  L.b.as<int16_t>(), in, out_fp64 ? nullptr : (float *)out,

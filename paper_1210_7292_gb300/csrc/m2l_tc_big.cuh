@@ -51,7 +51,8 @@ struct BigCfg {
     static constexpr int FIXED = 1024 + EG_ * 16 * FS * 4 + 2 * NT_ * 8 + EG_ * 2 * NT_ * 4 + 32 * 8;
     static constexpr int BUDGET = 225 * 1024;
     static constexpr int NB = (FIXED + 2 * B_STAGE + 3 * A_BLOCK <= BUDGET) ? 2 : 1;
-    static constexpr int RS = (FIXED + NB * B_STAGE + 4 * A_BLOCK <= BUDGET) ? 4 : 3;
+    static constexpr int RS = (FIXED + NB * B_STAGE + 4 * A_BLOCK <= BUDGET) ? 4
+                              : ((FIXED + NB * B_STAGE + 3 * A_BLOCK <= BUDGET) ? 3 : 2);
     static constexpr int SMEM = FIXED + NB * B_STAGE + RS * A_BLOCK;
     static constexpr int TMEM_COLS = (2 * MT * NT_ <= 128) ? 128 : ((2 * MT * NT_ <= 256) ? 256 : 512);
 };
@@ -338,6 +339,11 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
             tc_fence_after();
 #pragma unroll 1
             for (int ch = 0; ch < NT / 16; ++ch) {
+                // the chunk's table offsets in registers: read from shared memory inside
+                // the scatter below, each would wait for the previous store to sF
+                int go[16];
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) go[jj] = e_goff[16 * ch + jj];
 #pragma unroll 1
                 for (int mt = 0; mt < MT; ++mt) {
                     float v[16];
@@ -359,7 +365,7 @@ tc_big_kernel(const int2 *__restrict__ rec, const int *__restrict__ class_off, c
                     if (row < n3) {
 #pragma unroll
                         for (int jj = 0; jj < 16; ++jj)
-                            sF[jj * FS + __ldg(sinv_pad + e_goff[16 * ch + jj] + row)] = v[jj];
+                            sF[jj * FS + __ldg(sinv_pad + go[jj] + row)] = v[jj];
                     }
                 }
                 if constexpr (MODE == 1) continue;
@@ -468,6 +474,34 @@ template <int KIND, int MT, int KA>
 constexpr int real_eg()
 {
     return BigCfg<KIND, MT, KA, kBigNT, 2>::SMEM <= 227 * 1024 - 256 ? 2 : 1;
+}
+
+// Tile shape of the M2L for orders 6-8: the widest tile whose panel, ring and
+// epilogue fit, preferring two epilogue groups.  Each operator block streamed
+// from L2 and read by the tensor core then serves NT columns, so the A-operand
+// traffic per interaction falls as 1 / NT; a second epilogue group drains every
+// other tile.  Measured on GB300 at the 1/r^4 workload's level 6 (232 230
+// interactions): ell 7 BF16x3 0.54 -> 0.37 ms (64 x 2), TF32 0.51 -> 0.38 ms
+// (64 x 2), TF32x3 0.87 -> 0.63 ms (48 x 1); ell 8 BF16x3 0.88 -> 0.65 ms (48 x 1).
+template <int KIND, int MT, int KA, int NT, int EG>
+constexpr bool big_fits()
+{
+    return BigCfg<KIND, MT, KA, NT, EG>::SMEM <= 227 * 1024 - 256 && 2 * MT * NT <= 512;
+}
+
+template <int KIND, int MT, int KA>
+constexpr int big_nt()
+{
+    return big_fits<KIND, MT, KA, 64, 2>() ? 64
+         : (big_fits<KIND, MT, KA, 48, 2>() || big_fits<KIND, MT, KA, 48, 1>()) ? 48 : kBigNT;
+}
+
+template <int KIND, int MT, int KA>
+constexpr int big_eg()
+{
+    return big_fits<KIND, MT, KA, 64, 2>() ? 2
+         : big_fits<KIND, MT, KA, 48, 2>() ? 2
+         : big_fits<KIND, MT, KA, 48, 1>() ? 1 : real_eg<KIND, MT, KA>();
 }
 
 // The general form of the large-order kernel: ncls operator images of vector
