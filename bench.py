@@ -9,9 +9,10 @@ Multipole vectors are seeded N(0,1) stand-ins for the upward pass (the values
 do not change the work).
 
 One step = one pass of the whole hot path:
-  a1+a2  m2l_ops_rebuild      (16 operators and the permutation tables, on device)
-  a3     m2l_classify_level   (per level 2..5)
-  a4-a6  m2l_apply_classified (per level 2..5, the fused gather/GEMM/scatter kernel)
+  a2     m2l_ops_rebuild_tables     (the permutation tables, on device)
+  a1     m2l_ops_rebuild_operators  (the 16 operators) and m2l_ops_prepare (their kernel images)
+  a3     m2l_plan_classify          (per level 2..5, on the level's stream, after the tables)
+  a4-a6  m2l_plan_apply             (per level 2..5, the fused kernel, after the images)
 value = far-field interactions of levels 2..5 / step time, summed over ranks.
 """
 from __future__ import annotations
@@ -281,6 +282,20 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------------------------
+def rebuild_on(m2l, ops, precision, cur):
+    """Tables (a2), then operators (a1) and their kernel images, on stream `cur`;
+    returns the events after the tables (classification may start) and after the
+    images (applies may start)."""
+    import torch
+    tables, ready = torch.cuda.Event(), torch.cuda.Event()
+    m2l.m2l_ops_rebuild_tables(ops, cur)
+    tables.record(cur)
+    m2l.m2l_ops_rebuild_operators(ops, cur)
+    m2l.m2l_ops_prepare(ops, precision, cur)
+    ready.record(cur)
+    return tables, ready
+
+
 class Workload:
     def __init__(self, m2l, device, precision, seed):
         import numpy as np
@@ -317,25 +332,28 @@ class Workload:
         self.streams = {L: torch.cuda.Stream(device=device) for L in LEVELS}
         torch.cuda.synchronize(device)
 
+    def rebuild(self, cur):
+        return rebuild_on(self.m2l, self.ops, self.precision, cur)
+
     def step(self, kev=None):
-        """One pass of the hot path: operators and tables (a1, a2) on the current stream,
-        then per level, on its own stream, classification (a3) and the fused apply (a4-a6);
-        the current stream waits for every level."""
+        """One pass of the hot path: tables (a2) and operators (a1) on the current stream,
+        then per level, on its own stream, classification (a3, once the tables are done)
+        and the fused apply (a4-a6, once the operators are); the current stream waits for
+        every level."""
         import torch
         m2l = self.m2l
         cur = torch.cuda.current_stream(self.device)
-        m2l.m2l_ops_rebuild(self.ops, cur)
-        m2l.m2l_ops_prepare(self.ops, self.precision, cur)
-        ready = torch.cuda.Event()
-        ready.record(cur)
+        tables, ready = self.rebuild(cur)
         for L in sorted(LEVELS, reverse=True):   # the largest level first: it is the critical path
             s = self.streams[L]
-            s.wait_event(ready)
+            s.wait_event(tables)
             if kev is not None:
                 kev[L][2].record(s)
             m2l.m2l_plan_classify(self.plans[L], self.levels[L], s)
             if kev is not None:
                 kev[L][3].record(s)
+            s.wait_event(ready)
+            if kev is not None:
                 kev[L][0].record(s)
             m2l.m2l_plan_apply(self.plans[L], self.mp[L], self.loc[L], self.precision, stream=s)
             if kev is not None:
@@ -351,14 +369,11 @@ class Workload:
         import torch
         m2l = self.m2l
         cur = torch.cuda.current_stream(self.device)
-        m2l.m2l_ops_rebuild(self.ops, cur)
-        m2l.m2l_ops_prepare(self.ops, self.precision, cur)
-        ready = torch.cuda.Event()
-        ready.record(cur)
+        tables, ready = self.rebuild(cur)
         dev_lv = {}
         for L in sorted(LEVELS, reverse=True):   # the largest level first
             s = self.streams[L]
-            s.wait_event(ready)
+            s.wait_event(tables)
             h = self.host[L]
             with torch.cuda.stream(s):
                 ijk = h["ijk"].to(self.device, non_blocking=True)
@@ -368,6 +383,7 @@ class Workload:
                 lv = m2l.Level(2.0 / (1 << L), ijk, ijk, off, src, L)
                 loc = torch.zeros(lv.struct.ncells_tgt, ELL ** 3, dtype=self.dt_in, device=self.device)
                 m2l.m2l_plan_classify(self.plans[L], lv, s)
+                s.wait_event(ready)
                 m2l.m2l_plan_apply(self.plans[L], mp, loc, self.precision, stream=s)
                 h["loc"].copy_(loc, non_blocking=True)
             dev_lv[L] = (lv, mp, loc)
@@ -436,13 +452,10 @@ class ShardedWorkload:
         import torch
         m2l = self.m2l
         cur = torch.cuda.current_stream(self.device)
-        m2l.m2l_ops_rebuild(self.ops, cur)
-        m2l.m2l_ops_prepare(self.ops, self.precision, cur)
-        ready = torch.cuda.Event()
-        ready.record(cur)
+        tables, ready = rebuild_on(m2l, self.ops, self.precision, cur)
         for L in sorted(LEVELS, reverse=True):
             s = self.streams[L]
-            s.wait_event(ready)
+            s.wait_event(tables)
             with torch.cuda.stream(s):
                 halo = self.shard.exchange_multipoles(self.mine[L], self.ranges[L], self.sh[L]["needed"])
                 if kev is not None:
@@ -450,6 +463,8 @@ class ShardedWorkload:
                 m2l.m2l_plan_classify(self.plans[L], self.levels[L], s)
                 if kev is not None:
                     kev[L][3].record(s)
+                s.wait_event(ready)
+                if kev is not None:
                     kev[L][0].record(s)
                 m2l.m2l_plan_apply(self.plans[L], halo, self.loc[L], self.precision, stream=s)
                 if kev is not None:
@@ -464,14 +479,11 @@ class ShardedWorkload:
         import torch
         m2l = self.m2l
         cur = torch.cuda.current_stream(self.device)
-        m2l.m2l_ops_rebuild(self.ops, cur)
-        m2l.m2l_ops_prepare(self.ops, self.precision, cur)
-        ready = torch.cuda.Event()
-        ready.record(cur)
+        tables, ready = rebuild_on(m2l, self.ops, self.precision, cur)
         keep = {}
         for L in sorted(LEVELS, reverse=True):
             s = self.streams[L]
-            s.wait_event(ready)
+            s.wait_event(tables)
             h = self.host[L]
             with torch.cuda.stream(s):
                 mine = h["mine"].to(self.device, non_blocking=True)
@@ -481,6 +493,7 @@ class ShardedWorkload:
                 halo = self.shard.exchange_multipoles(mine, self.ranges[L], self.sh[L]["needed"])
                 loc = torch.zeros(lv.struct.ncells_tgt, ELL ** 3, dtype=self.dt_in, device=self.device)
                 m2l.m2l_plan_classify(self.plans[L], lv, s)
+                s.wait_event(ready)
                 m2l.m2l_plan_apply(self.plans[L], halo, loc, self.precision, stream=s)
                 h["loc"].copy_(loc, non_blocking=True)
             keep[L] = (lv, mine, halo, loc)

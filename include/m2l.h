@@ -172,6 +172,17 @@ m2l_status m2l_ops_aca_info(const m2l_ops *ops, int32_t *aca_terms16, int32_t *j
  * eps > 0. */
 m2l_status m2l_ops_rebuild(m2l_ops *ops, void *stream);
 
+/* m2l_ops_rebuild in two parts, for a step that classifies its levels while
+ * the operators are assembled: m2l_ops_rebuild_tables re-runs the tables of
+ * Sec. 4.2.1 (sigma_g, the t -> (p, g) table, T_sym: all that classification
+ * reads), m2l_ops_rebuild_operators the assembly of the 16 operators
+ * (Eq. (15), which reads T_sym), so it must follow the tables in stream order.
+ * Classification of a level may run on another stream once the tables are
+ * done; an apply needs both parts (and m2l_ops_prepare) done.  Same rules and
+ * errors as m2l_ops_rebuild. */
+m2l_status m2l_ops_rebuild_tables(m2l_ops *ops, void *stream);
+m2l_status m2l_ops_rebuild_operators(m2l_ops *ops, void *stream);
+
 /* Host copies of the tables, for checking (Sec. 4.2.1).  Any output may be
  * NULL.  ranks16: [16] ranks r_p (ell^3 when full rank).  sigma48: [48][ell^3]
  * with sigma48[g][j] = m(pi_g(m^{-1}(j))), g = 8 * perm_id + flip_mask where

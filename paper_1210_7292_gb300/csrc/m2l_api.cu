@@ -261,19 +261,29 @@ m2l_status precompute_impl(m2l_kernel kernel, int ell, double eps, double width,
 
 extern "C" {
 
-m2l_status m2l_ops_rebuild(m2l_ops *ops, void *stream)
+namespace {
+m2l_status rebuild_part(m2l_ops *ops, void *stream, bool tables, bool operators)
 {
     if (!ops) { set_error("null ops"); return M2L_EINVAL; }
     if (ops->eps > 0) { set_error("rebuild of low-rank operators is not supported"); return M2L_EUNSUPPORTED; }
+    m2l_status st = check_device(ops);
+    if (st != M2L_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    m2l_status st = build_tables(ops, s);
-    if (st == M2L_OK) st = assemble_operators(ops, s);
+    if (tables) st = build_tables(ops, s);
+    if (st == M2L_OK && operators) st = assemble_operators(ops, s);
     // derived layouts are rebuilt from the new masters on their next use
     ops->simt64.ready = ops->simt32.ready = false;
     ops->tc_tf32.ready = ops->tc_bf16x3.ready = ops->tc_tf32x3.ready = false;
     ops->tcd_tf32.ready = ops->tcd_bf16x3.ready = ops->tcd_tf32x3.ready = false;
     return st;
 }
+}  // namespace
+
+m2l_status m2l_ops_rebuild(m2l_ops *ops, void *stream) { return rebuild_part(ops, stream, true, true); }
+
+m2l_status m2l_ops_rebuild_tables(m2l_ops *ops, void *stream) { return rebuild_part(ops, stream, true, false); }
+
+m2l_status m2l_ops_rebuild_operators(m2l_ops *ops, void *stream) { return rebuild_part(ops, stream, false, true); }
 
 m2l_status m2l_ops_query(const m2l_ops *ops, int *ranks16, int16_t *sigma48, uint16_t *lut343)
 {

@@ -61,6 +61,8 @@ def lib():
         sig = {
             "m2l_precompute": [m2l_kernel, I, D, D, ctypes.POINTER(P)],
             "m2l_ops_rebuild": [P, P],
+            "m2l_ops_rebuild_tables": [P, P],
+            "m2l_ops_rebuild_operators": [P, P],
             "m2l_ops_query": [P, P, P, P],
             "m2l_ops_copy_operators": [P, P],
             "m2l_ops_copy_lowrank": [P, I, P, P],
@@ -259,6 +261,14 @@ def m2l_ops_aca_info(ops: Ops):
 
 def m2l_ops_rebuild(ops: Ops, stream=None):
     _check("m2l_ops_rebuild", lib().m2l_ops_rebuild(ops.handle, _stream_ptr(stream, ops.device)))
+
+
+def m2l_ops_rebuild_tables(ops: Ops, stream=None):
+    _check("m2l_ops_rebuild_tables", lib().m2l_ops_rebuild_tables(ops.handle, _stream_ptr(stream, ops.device)))
+
+
+def m2l_ops_rebuild_operators(ops: Ops, stream=None):
+    _check("m2l_ops_rebuild_operators", lib().m2l_ops_rebuild_operators(ops.handle, _stream_ptr(stream, ops.device)))
 
 
 def m2l_ops_query(ops: Ops):

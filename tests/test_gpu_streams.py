@@ -21,10 +21,13 @@ def m2l():
     return mod
 
 
+@pytest.mark.parametrize("split", [False, True])
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3", "tf32x3"])
-def test_levels_on_concurrent_streams(m2l, prec):
+def test_levels_on_concurrent_streams(m2l, prec, split):
     """Levels 2-4 of a pruned tree, ell = 4, 1/r (one homogeneous operator set),
-    classified and applied on three streams at once, twice in a row."""
+    classified and applied on three streams at once, twice in a row.  With
+    split, the levels classify as soon as the tables are rebuilt, while the
+    operators are assembled and prepared on the current stream."""
     ell = 4
     ops = gpu_ops(m2l, ell, 0, 2)
     data = {}
@@ -38,17 +41,24 @@ def test_levels_on_concurrent_streams(m2l, prec):
     outs = {}
     for rep in range(2):
         cur = torch.cuda.current_stream()
-        m2l.m2l_ops_rebuild(ops, cur)
+        tables = torch.cuda.Event()
+        if split:
+            m2l.m2l_ops_rebuild_tables(ops, cur)
+            tables.record(cur)
+            m2l.m2l_ops_rebuild_operators(ops, cur)
+        else:
+            m2l.m2l_ops_rebuild(ops, cur)
         m2l.m2l_ops_prepare(ops, prec, cur)
         ready = torch.cuda.Event()
         ready.record(cur)
         for L, (cells, w, lv) in data.items():
             s = streams[L]
-            s.wait_event(ready)
+            s.wait_event(tables if split else ready)
             with torch.cuda.stream(s):
                 outs[L] = torch.zeros(len(cells), ell ** 3, dtype=torch.float32, device=device())
                 win = torch.from_numpy(w).to(device(), torch.float32)
             m2l.m2l_plan_classify(plans[L], lv, s)
+            s.wait_event(ready)
             m2l.m2l_plan_apply(plans[L], win, outs[L], prec, stream=s)
             done = torch.cuda.Event()
             done.record(s)
