@@ -383,13 +383,14 @@ __device__ __forceinline__ int job_entry(int j, int ns)
     }
 }
 
-constexpr int kDenseProdWarps = 4;                                        // warps 0-3: producers
-constexpr int kDenseMmaWarp = 4;
-constexpr int kDenseEpiWarp0 = 5;
+constexpr int kDenseProdWarps = 8;                                        // warps 0-7: producers
+constexpr int kDenseMmaWarp = 8;
+constexpr int kDenseEpiWarp0 = 9;
 constexpr int kDenseEpiWarps = 16;
 constexpr int kDenseThreads = (kDenseEpiWarp0 + kDenseEpiWarps) * 32;
 constexpr int kDenseGroupsPerWarp = 4;                                    // 16-column groups, nu <= 256
-constexpr int kDenseMaxColM = 16;                                         // panel columns per producer thread (nu <= 256)
+constexpr int kDenseColStride = kDenseProdWarps * 4;                      // columns per pass of the producers (8 threads a column)
+constexpr int kDenseMaxColM = 256 / kDenseColStride;                      // panel columns per producer thread (nu <= 256)
 constexpr int kDenseMaxStages = 4;
 constexpr int kDenseDStride = 256;    // TMEM columns between the two accumulators
 
@@ -470,7 +471,7 @@ tc_dense_kernel(const uint8_t *__restrict__ bsplit, const uint8_t *__restrict__ 
         // the next group's are read after its last stage.
         const int pt = threadIdx.x;
         const int cb = pt >> 3, kc = pt & 7;
-        const int ncm = nu >> 4;                  // columns of this thread
+        const int ncm = (nu - cb + kDenseColStride - 1) / kDenseColStride;   // columns of this thread
         const size_t row_bytes = (size_t)Tr::nparts * kpad * Tr::esz;
         const uint8_t *src_base = bsplit + kc * 16;
         long it = 0;
@@ -485,7 +486,7 @@ tc_dense_kernel(const uint8_t *__restrict__ bsplit, const uint8_t *__restrict__ 
                 const int32_t *t = utab + (size_t)slot * nu;
 #pragma unroll
                 for (int m = 0; m < kDenseMaxColM; ++m) {
-                    const int e = (m < ncm) ? __ldg(t + 16 * m) : 0;
+                    const int e = (m < ncm) ? __ldg(t + kDenseColStride * m) : 0;
                     v[m] = e ? e - 1 : nsrc;
                 }
             };
@@ -522,7 +523,7 @@ tc_dense_kernel(const uint8_t *__restrict__ bsplit, const uint8_t *__restrict__ 
 #pragma unroll
                         for (int m = 0; m < kDenseMaxColM; ++m) {
                             if (m < ncm) {
-                                const int c = cb + 16 * m;
+                                const int c = cb + kDenseColStride * m;
                                 const uint32_t off = (uint32_t)((c >> 3) * 1024 + (c & 7) * 128 + ((kc ^ (c & 7)) << 4));
                                 const uint8_t *src = src_k + (size_t)(j ? yB[m] : yA[m]) * row_bytes;
 #pragma unroll
