@@ -402,7 +402,7 @@ __host__ __device__ constexpr int dense_stage_bytes(int nu)
 }
 
 // One persistent CTA per SM over units blockIdx.x, blockIdx.x + gridDim.x, ...
-// Warps 0-3 producers, warp 4 MMA, warps 5-20 epilogue.
+// Warps 0-7 producers, warp 8 MMA, warps 9-24 epilogue.
 template <int KIND>
 __global__ void __launch_bounds__(kDenseThreads, 1)
 tc_dense_kernel(const uint8_t *__restrict__ bsplit, const uint8_t *__restrict__ a_img,
@@ -461,8 +461,8 @@ tc_dense_kernel(const uint8_t *__restrict__ bsplit, const uint8_t *__restrict__ 
 
     if (warp < kDenseProdWarps) {
         // ---------------------------------------------------------- producers
-        // Thread t of the 128 copies, per stage, the 16-byte chunk t % 8 of the
-        // 128-byte K column of columns t / 8 + 16 m (every part) from the split
+        // Thread t of the 256 copies, per stage, the 16-byte chunk t % 8 of the
+        // 128-byte K column of columns t / 8 + 32 m (every part) from the split
         // multipole rows straight to its 128-byte-swizzled place in the operand
         // panel (cp.async through L1), then arms the stage's panel barrier with
         // an arrive that fires when its copies have landed.  Thread 0 also copies
