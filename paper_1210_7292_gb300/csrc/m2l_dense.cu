@@ -121,15 +121,25 @@ __global__ void dense_place_kernel(int ntgt, int nblk, int nu, const int32_t *__
 // One warp per target row of the CSR list: each entry (X, Y) writes Y + 1 into
 // tab[unit(X)][slot(t)][column(X)] and flags the slot of the unit.  Entries
 // that are not far-field pairs, indices out of range and repeated (X, t) pairs
-// set the status word and are skipped.
-__global__ void dense_fill_kernel(int ntgt, int nsrc, int nnz, int nu, const int32_t *__restrict__ offsets,
-                                  const int32_t *__restrict__ sources, const int32_t *__restrict__ tgt_ijk,
-                                  const int32_t *__restrict__ src_ijk, const uint16_t *__restrict__ lut,
-                                  const int32_t *__restrict__ unit_col, int32_t *__restrict__ tab,
-                                  int32_t *__restrict__ flags, int *__restrict__ status)
+// set the status word and are skipped.  A row's slots are marked in a bit set
+// in shared memory, so the table takes plain stores (a repeated (X, t) is found
+// in the row, the only place it can occur).
+constexpr int kFillThreads = 256;
+constexpr int kSlotWords = (kSlots + 31) / 32;
+
+__global__ void __launch_bounds__(kFillThreads)
+dense_fill_kernel(int ntgt, int nsrc, int nnz, int nu, const int32_t *__restrict__ offsets,
+                  const int32_t *__restrict__ sources, const int32_t *__restrict__ tgt_ijk,
+                  const int32_t *__restrict__ src_ijk, const uint16_t *__restrict__ lut,
+                  const int32_t *__restrict__ unit_col, int32_t *__restrict__ tab, int32_t *__restrict__ flags,
+                  int *__restrict__ status)
 {
+    __shared__ unsigned seen_all[kFillThreads / 32][kSlotWords];
     const int x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
+    unsigned *seen = seen_all[threadIdx.x >> 5];
+    if (lane < kSlotWords) seen[lane] = 0u;
+    __syncwarp();
     if (x >= ntgt) return;
     const int o0 = offsets[x], o1 = offsets[x + 1];
     if (o0 < 0 || o1 < o0 || o1 > nnz || (x == 0 && o0 != 0)) {
@@ -155,8 +165,12 @@ __global__ void dense_fill_kernel(int ntgt, int nsrc, int nnz, int nu, const int
             atomicOr(status, ST_BAD_PAIR);
             continue;
         }
-        const int prev = atomicExch(tab + ((size_t)u * kSlots + slot) * nu + j, y + 1);
-        if (prev != 0) atomicOr(status, ST_BAD_PAIR);   // the same (X, t) twice
+        const unsigned bit = 1u << (slot & 31);
+        if (atomicOr(seen + (slot >> 5), bit) & bit) {   // the same (X, t) twice
+            atomicOr(status, ST_BAD_PAIR);
+            continue;
+        }
+        tab[((size_t)u * kSlots + slot) * nu + j] = y + 1;
         flags[(size_t)u * kSlots + slot] = 1;
     }
 }
@@ -260,8 +274,8 @@ m2l_status dense_classify(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const
                                                            unit_col, d.unit_tgt.as<int32_t>());
     M2L_LAUNCH_CHECK("dense_place_kernel");
     if (nnz > 0) {
-        const int blocks = (int)(((long)ntgt * 32 + 255) / 256);
-        dense_fill_kernel<<<blocks, 256, 0, s>>>(ntgt, nsrc, nnz, nu, offsets, sources, tgt_ijk, src_ijk,
+        const int blocks = (int)(((long)ntgt * 32 + kFillThreads - 1) / kFillThreads);
+        dense_fill_kernel<<<blocks, kFillThreads, 0, s>>>(ntgt, nsrc, nnz, nu, offsets, sources, tgt_ijk, src_ijk,
                                                  ops->lut.as<uint16_t>(), unit_col, d.tab.as<int32_t>(), flags,
                                                  ops->d_status);
         M2L_LAUNCH_CHECK("dense_fill_kernel");

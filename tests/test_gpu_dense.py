@@ -190,6 +190,40 @@ def test_dense_bounded_wait_reports_timeout(m2l):
     _check(_plan_apply(m2l, plan, w, "bf16x3", len(cells)), ref, "bf16x3")
 
 
+def test_dense_repeated_and_near_entries_reported(m2l):
+    """On the dense path a repeated (X, t) entry and a near-field entry are
+    skipped and reported (M2L_EINVAL); every other entry is applied."""
+    from paper_1210_7292_gb300 import synth
+    ell, level = 2, 5
+    cells = synth.full_grid(level)
+    off, src = _lists(cells)
+    bad = src.copy()
+    r1, r2 = 100, 20000
+    bad[off[r1] + 1] = src[off[r1]]                    # row r1: its first (X, t) twice
+    nb = cells[r2] + np.array([1, 0, 0]) if cells[r2][0] < (1 << level) - 1 else cells[r2] - np.array([1, 0, 0])
+    near = int(np.flatnonzero((cells == nb).all(axis=1))[0])
+    bad[off[r2]] = near                                # row r2: a near-field neighbour
+    keep = np.ones(len(src), dtype=bool)
+    keep[[off[r1] + 1, off[r2]]] = False
+    good_off = np.concatenate([[0], np.cumsum([keep[off[i]:off[i + 1]].sum() for i in range(len(cells))])])
+    good_src = src[keep]
+    ijk = torch.from_numpy(np.ascontiguousarray(cells, dtype=np.int32)).to(device())
+    lv = m2l.Level(oracle.cell_width(level), ijk, ijk, torch.from_numpy(off).to(device()),
+                   torch.from_numpy(bad).to(device()), level)
+    ops = gpu_ops(m2l, ell, 0, level)
+    plan = m2l.m2l_plan_create(ops, lv)
+    assert m2l.m2l_plan_kernel_info(plan)["dense"]
+    w = synth.gaussian_vectors(len(cells), ell ** 3, seed=306)
+    loc = torch.zeros(len(cells), ell ** 3, dtype=torch.float32, device=device())
+    m2l.m2l_plan_apply(plan, torch.from_numpy(w).to(device(), torch.float32), loc, "bf16x3")
+    with pytest.raises(m2l.M2LError) as ei:
+        m2l.m2l_sync_status(ops)
+    assert ei.value.status == m2l.M2L_EINVAL
+    ref = oracle.m2l_apply(oracle_ops(ell, 0, level), cells, cells, good_off.astype(np.int32), good_src, w)
+    _check(loc.cpu().double().numpy(), ref, "bf16x3")
+    m2l.m2l_sync_status(ops)   # cleared
+
+
 @pytest.mark.parametrize("adjoint", [False, True])
 def test_buckets_derived_from_dense_classification(m2l, adjoint):
     """A full level is classified for the dense kernel only; asking for its
