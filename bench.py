@@ -282,6 +282,13 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------------------------
+def level_streams(device):
+    """One stream per level; the largest level's, the step's critical path, at high
+    priority so that its classification and apply go ahead of the smaller levels'."""
+    import torch
+    return {L: torch.cuda.Stream(device=device, priority=-1 if L == max(LEVELS) else 0) for L in LEVELS}
+
+
 def rebuild_on(m2l, ops, precision, cur):
     """Tables (a2), then operators (a1) and their kernel images, on stream `cur`;
     returns the events after the tables (classification may start) and after the
@@ -329,7 +336,7 @@ class Workload:
         # locals, so the levels run concurrently: one stream and one plan (its own bucket
         # buffers) per level, classified again in every step
         self.plans = {L: m2l.m2l_plan_create(self.ops, self.levels[L]) for L in LEVELS}
-        self.streams = {L: torch.cuda.Stream(device=device) for L in LEVELS}
+        self.streams = level_streams(device)
         torch.cuda.synchronize(device)
 
     def rebuild(self, cur):
@@ -445,7 +452,7 @@ class ShardedWorkload:
         self.total = sum(self.nint.values())
         self.local_nint = {L: self.levels[L].nnz for L in LEVELS}
         self.plans = {L: m2l.m2l_plan_create(self.ops, self.levels[L]) for L in LEVELS}
-        self.streams = {L: torch.cuda.Stream(device=device) for L in LEVELS}
+        self.streams = level_streams(device)
         torch.cuda.synchronize(device)
 
     def step(self, kev=None):
