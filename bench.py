@@ -337,6 +337,7 @@ class Workload:
         # buffers) per level, classified again in every step
         self.plans = {L: m2l.m2l_plan_create(self.ops, self.levels[L]) for L in LEVELS}
         self.streams = level_streams(device)
+        self.copy_streams = {L: torch.cuda.Stream(device=device) for L in LEVELS}
         torch.cuda.synchronize(device)
 
     def rebuild(self, cur):
@@ -386,10 +387,20 @@ class Workload:
                 ijk = h["ijk"].to(self.device, non_blocking=True)
                 off = h["off"].to(self.device, non_blocking=True)
                 src = h["src"].to(self.device, non_blocking=True)
-                mp = h["mp"].to(self.device, non_blocking=True)
                 lv = m2l.Level(2.0 / (1 << L), ijk, ijk, off, src, L)
                 loc = torch.zeros(lv.struct.ncells_tgt, ELL ** 3, dtype=self.dt_in, device=self.device)
                 m2l.m2l_plan_classify(self.plans[L], lv, s)
+            # the multipoles are read by the apply only: they are copied on a stream of
+            # their own, beside the lists' copies and the classification
+            c = self.copy_streams[L]
+            c.wait_event(tables)   # within this step, as every other copy
+            with torch.cuda.stream(c):
+                mp = h["mp"].to(self.device, non_blocking=True)
+            mp.record_stream(s)
+            mp_done = torch.cuda.Event()
+            mp_done.record(c)
+            with torch.cuda.stream(s):
+                s.wait_event(mp_done)
                 s.wait_event(ready)
                 m2l.m2l_plan_apply(self.plans[L], mp, loc, self.precision, stream=s)
                 h["loc"].copy_(loc, non_blocking=True)
