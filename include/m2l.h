@@ -125,9 +125,10 @@ typedef struct {
  *    table t -> (p, g);
  *  - when eps > 0, a truncated SVD of each K_p, K_p ~ (U_p Sigma_p) V_p^T
  *    (Eq. (20)), at the rank the truncation criterion gives (M2L_TRUNC_FROBENIUS
- *    here; m2l_precompute_ex chooses).  The SVD is one-sided Jacobi on the
- *    device (FP64, rotations of column pairs in round-robin order until every
- *    pair is orthogonal to 1e-12 relative to the columns' norms).
+ *    here; m2l_precompute_ex chooses).  The SVD runs on the device in FP64:
+ *    Householder QR with column pivoting of K_p^T, then one-sided Jacobi on
+ *    R^T (rotations of column pairs in round-robin order until every pair is
+ *    orthogonal to 1e-12 relative to the columns' norms).
  * ell: Chebyshev order, 2 <= ell <= 8.  eps: 0 for full rank, else in (0, 1).
  * width: cell width for the non-homogeneous kernel (ignored otherwise).
  * out: receives a new m2l_ops; free with m2l_ops_free.

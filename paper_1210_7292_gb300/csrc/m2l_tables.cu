@@ -113,37 +113,199 @@ __global__ void assemble_kernel(int ell, int kind, double c, double w, const int
 
 // U_p = U_K Sigma (first r_p columns), V_p = V_K, both [n3][rmax] row-major,
 // from the column-major SVD M = U_M S V_M^T of M = K_p^T (so U_K = V_M, V_K = U_M).
-// A[p] = K_p^T stored row-major, i.e. K_p column-major: column j of K_p contiguous.
-__global__ void to_column_major_kernel(int n3, const double *__restrict__ K, double *__restrict__ A)
+// ---------------------------------------------------------------- step a1's SVD
+// The truncated SVD of each K_p (Eq. (20)) as a QR-preconditioned one-sided
+// Jacobi SVD (Drmac and Veselic): M = K_p^T (the row-major K_p read column-major)
+// is factored M P = Q R by Householder QR with column pivoting, R^T by
+// one-sided Jacobi, R^T V_J = W Sigma.  Then K_p = P R^T Q^T = (P W Sigma)(Q V_J)^T:
+// U_p = (P W Sigma)_r, V_p = (Q V_J)_r.  The pivoting concentrates the norms on
+// R's leading rows, so Jacobi on R^T converges in a handful of sweeps instead
+// of the dozens it takes on K_p itself.
+constexpr int kQrThreads = 512;
+constexpr int kQrWarps = kQrThreads / 32;
+
+__device__ __forceinline__ double qr_warp_sum(double v)
 {
-    const long nn = (long)n3 * n3, total = 16 * nn;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-        const long p = i / nn, r = i % nn, col = r / n3, row = r % n3;
-        A[i] = K[p * nn + row * n3 + col];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One block per matrix: A [p] column-major n x n (in place: R on and above the
+// diagonal, the Householder vectors' tails below it), vhead [p][n] their first
+// entries, beta [p][n] = 2 / (v^T v) (0 for a zero column), perm [p][n]: column k
+// of M P is column perm[k] of M.
+__global__ void __launch_bounds__(kQrThreads)
+qrcp_kernel(int n, double *__restrict__ A, double *__restrict__ vhead, double *__restrict__ beta,
+            int *__restrict__ perm)
+{
+    extern __shared__ double qr_smem[];
+    double *cn = qr_smem;                              // [n] column norms^2 of the trailing block
+    __shared__ double s_val[kQrWarps];
+    __shared__ int s_idx[kQrWarps];
+    __shared__ double s_alpha, s_v0, s_beta;
+    __shared__ int s_piv;
+    const int p = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *M = A + (size_t)p * n * n;
+    int *pm = perm + (size_t)p * n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) pm[j] = j;
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        // 1. norms^2 of columns k..n-1 over rows k..n-1
+        for (int j = k + warp; j < n; j += kQrWarps) {
+            const double *c = M + (size_t)j * n;
+            double s2 = 0.0;
+            for (int i = k + lane; i < n; i += 32) s2 += c[i] * c[i];
+            s2 = qr_warp_sum(s2);
+            if (lane == 0) cn[j] = s2;
+        }
+        __syncthreads();
+        // 2. the pivot: the largest norm, the first column on ties
+        double bv = -1.0;
+        int bi = n;
+        for (int j = k + threadIdx.x; j < n; j += blockDim.x)
+            if (cn[j] > bv) {
+                bv = cn[j];
+                bi = j;
+            }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            s_val[warp] = bv;
+            s_idx[warp] = bi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double v = s_val[0];
+            int ix = s_idx[0];
+            for (int w = 1; w < kQrWarps; ++w)
+                if (s_val[w] > v || (s_val[w] == v && s_idx[w] < ix)) {
+                    v = s_val[w];
+                    ix = s_idx[w];
+                }
+            s_piv = ix < n ? ix : k;
+        }
+        __syncthreads();
+        const int piv = s_piv;
+        // 3. swap columns k and piv (all rows: the rows above k hold R)
+        if (piv != k) {
+            double *ck = M + (size_t)k * n, *cp = M + (size_t)piv * n;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const double t = ck[i];
+                ck[i] = cp[i];
+                cp[i] = t;
+            }
+            if (threadIdx.x == 0) {
+                const int t = pm[k];
+                pm[k] = pm[piv];
+                pm[piv] = t;
+                const double tn = cn[k];
+                cn[k] = cn[piv];
+                cn[piv] = tn;
+            }
+        }
+        __syncthreads();
+        // 4. the Householder reflector of column k: H x = alpha e_k
+        if (threadIdx.x == 0) {
+            const double x0 = M[(size_t)k * n + k];
+            const double nx = sqrt(cn[k]);
+            const double alpha = x0 >= 0.0 ? -nx : nx;
+            const double v0 = x0 - alpha;
+            const double vtv = cn[k] - x0 * x0 + v0 * v0;
+            s_alpha = alpha;
+            s_v0 = v0;
+            s_beta = vtv > 0.0 ? 2.0 / vtv : 0.0;
+        }
+        __syncthreads();
+        const double v0 = s_v0, bk = s_beta;
+        const double *vk = M + (size_t)k * n;   // tail entries vk[i], i > k
+        // 5. apply it to the columns k+1..n-1
+        for (int j = k + 1 + warp; j < n; j += kQrWarps) {
+            double *c = M + (size_t)j * n;
+            double d = 0.0;
+            for (int i = k + 1 + lane; i < n; i += 32) d += vk[i] * c[i];
+            d = qr_warp_sum(d) + v0 * c[k];
+            const double w = bk * d;
+            __syncwarp();   // every lane has read c[k]
+            if (lane == 0) c[k] -= w * v0;
+            for (int i = k + 1 + lane; i < n; i += 32) c[i] -= w * vk[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            M[(size_t)k * n + k] = s_alpha;
+            vhead[(size_t)p * n + k] = v0;
+            beta[(size_t)p * n + k] = bk;
+        }
+        __syncthreads();
     }
 }
 
-// After the one-sided Jacobi SVD K_p V = W Sigma (A holds W Sigma column-major):
-// U[p][row][q] = (W Sigma)(row, order_q), V[p][row][q] = V(row, order_q) for
-// q < r_p, zero beyond (the [16][n3][rmax] layout of the factors).
-__global__ void extract_lowrank_kernel(int n3, int rmax, const int *__restrict__ ranks, const int *__restrict__ order,
-                                       const double *__restrict__ A, const double *__restrict__ Vr,
-                                       double *__restrict__ U, double *__restrict__ V)
+// B [p] column-major = R^T: column j holds row j of R (R(j, i), i >= j), zeros above.
+__global__ void r_transpose_kernel(int n, const double *__restrict__ A, double *__restrict__ B)
+{
+    const long nn = (long)n * n, total = 16 * nn;
+    for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < total; x += (long)gridDim.x * blockDim.x) {
+        const long p = x / nn, r = x % nn, j = r / n, i = r % n;
+        B[x] = i >= j ? A[p * nn + i * n + j] : 0.0;
+    }
+}
+
+// U[p][perm[k]][q] = (W Sigma)(k, order_q) for q < r_p, zero beyond.
+__global__ void extract_u_kernel(int n3, int rmax, const int *__restrict__ ranks, const int *__restrict__ order,
+                                 const int *__restrict__ perm, const double *__restrict__ B, double *__restrict__ U)
 {
     const int p = blockIdx.y;
     const int r = ranks[p];
     const long nn = (long)n3 * n3;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n3 * rmax; idx += gridDim.x * blockDim.x) {
-        const int row = idx / rmax, k = idx % rmax;
-        double u = 0.0, v = 0.0;
-        if (k < r) {
-            const long col = order[p * n3 + k];
-            u = A[p * nn + col * n3 + row];
-            v = Vr[p * nn + col * n3 + row];
-        }
-        U[(long)p * n3 * rmax + idx] = u;
-        V[(long)p * n3 * rmax + idx] = v;
+        const int k = idx / rmax, q = idx % rmax;
+        const double u = q < r ? B[p * nn + (long)order[p * n3 + q] * n3 + k] : 0.0;
+        U[((long)p * n3 + perm[p * n3 + k]) * rmax + q] = u;
     }
+}
+
+// V[p][:, q] = Q V_J[:, order_q] = H_0 H_1 ... H_{n-1} V_J[:, order_q] for q < r_p, zero
+// beyond; one warp per column, the column in shared memory.
+constexpr int kQWarps = 8;
+__global__ void __launch_bounds__(kQWarps * 32)
+apply_q_kernel(int n, int rmax, const int *__restrict__ ranks, const int *__restrict__ order,
+               const double *__restrict__ A, const double *__restrict__ vhead, const double *__restrict__ beta,
+               const double *__restrict__ VJ, double *__restrict__ V)
+{
+    extern __shared__ double q_smem[];
+    const int p = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = blockIdx.x * kQWarps + warp;
+    if (q >= rmax) return;
+    const long nn = (long)n * n;
+    double *x = q_smem + (size_t)warp * n;
+    if (q >= ranks[p]) {
+        for (int i = lane; i < n; i += 32) V[((long)p * n + i) * rmax + q] = 0.0;
+        return;
+    }
+    const double *src = VJ + p * nn + (long)order[p * n + q] * n;
+    for (int i = lane; i < n; i += 32) x[i] = src[i];
+    __syncwarp();
+    const double *M = A + p * nn;
+    for (int k = n - 1; k >= 0; --k) {
+        const double bk = beta[(long)p * n + k];
+        if (bk == 0.0) continue;
+        const double v0 = vhead[(long)p * n + k];
+        const double *vk = M + (long)k * n;
+        double d = 0.0;
+        for (int i = k + 1 + lane; i < n; i += 32) d += vk[i] * x[i];
+        d = qr_warp_sum(d) + v0 * x[k];
+        const double w = bk * d;
+        __syncwarp();
+        if (lane == 0) x[k] -= w * v0;
+        for (int i = k + 1 + lane; i < n; i += 32) x[i] -= w * vk[i];
+        __syncwarp();
+    }
+    for (int i = lane; i < n; i += 32) V[((long)p * n + i) * rmax + q] = x[i];
 }
 
 template <typename T>
@@ -208,24 +370,33 @@ m2l_status assemble_operators(m2l_ops *ops, cudaStream_t s)
     return M2L_OK;
 }
 
-// Step a1's truncated SVD of the 16 operators (Eq. (20)), by one-sided Jacobi
-// on the device; ranks by the ops' truncation criterion.
+// Step a1's truncated SVD of the 16 operators (Eq. (20)), QR-preconditioned
+// one-sided Jacobi on the device; ranks by the ops' truncation criterion.
 m2l_status lowrank_factors(m2l_ops *ops)
 {
     const int n = ops->n3;
     const size_t nn = (size_t)n * n;
-    DevBuf A, S, VR, dord, dranks;
-    ScratchGuard guard{&A, &S, &VR, &dord, &dranks};
+    DevBuf A, B, S, VJ, vh, bt, pm, dord, dranks;
+    ScratchGuard guard{&A, &B, &S, &VJ, &vh, &bt, &pm, &dord, &dranks};
     m2l_status st;
     if ((st = A.ensure(16 * nn * sizeof(double))) != M2L_OK) return st;
+    if ((st = B.ensure(16 * nn * sizeof(double))) != M2L_OK) return st;
+    if ((st = VJ.ensure(16 * nn * sizeof(double))) != M2L_OK) return st;
     if ((st = S.ensure(16 * (size_t)n * sizeof(double))) != M2L_OK) return st;
-    if ((st = VR.ensure(16 * nn * sizeof(double))) != M2L_OK) return st;
+    if ((st = vh.ensure(16 * (size_t)n * sizeof(double))) != M2L_OK) return st;
+    if ((st = bt.ensure(16 * (size_t)n * sizeof(double))) != M2L_OK) return st;
+    if ((st = pm.ensure(16 * (size_t)n * sizeof(int))) != M2L_OK) return st;
     if ((st = dord.ensure(16 * (size_t)n * sizeof(int))) != M2L_OK) return st;
     if ((st = dranks.ensure(16 * sizeof(int))) != M2L_OK) return st;
-    to_column_major_kernel<<<(int)std::min<size_t>((16 * nn + 255) / 256, 65535), 256>>>(n, ops->K64.as<double>(),
-                                                                                         A.as<double>());
-    M2L_LAUNCH_CHECK("to_column_major_kernel");
-    if ((st = jacobi_svd(A.as<double>(), n, n, 16, VR.as<double>(), S.as<double>(), ops->jacobi_sweeps, 0)) != M2L_OK)
+    // M = K_p^T column-major is K_p's row-major memory
+    M2L_CUDA(cudaMemcpy(A.p, ops->K64.p, 16 * nn * sizeof(double), cudaMemcpyDeviceToDevice));
+    qrcp_kernel<<<16, kQrThreads, (size_t)n * sizeof(double)>>>(n, A.as<double>(), vh.as<double>(), bt.as<double>(),
+                                                                pm.as<int>());
+    M2L_LAUNCH_CHECK("qrcp_kernel");
+    r_transpose_kernel<<<(int)std::min<size_t>((16 * nn + 255) / 256, 65535), 256>>>(n, A.as<double>(),
+                                                                                    B.as<double>());
+    M2L_LAUNCH_CHECK("r_transpose_kernel");
+    if ((st = jacobi_svd(B.as<double>(), n, n, 16, VJ.as<double>(), S.as<double>(), ops->jacobi_sweeps, 0)) != M2L_OK)
         return st;
     std::vector<double> hS(16 * (size_t)n), sorted(n);
     std::vector<int> hord(16 * (size_t)n);
@@ -245,10 +416,13 @@ m2l_status lowrank_factors(m2l_ops *ops)
     if ((st = ops->V64.ensure(16 * (size_t)n * rmax * sizeof(double))) != M2L_OK) return st;
     M2L_CUDA(cudaMemcpy(dranks.p, ops->ranks, 16 * sizeof(int), cudaMemcpyHostToDevice));
     M2L_CUDA(cudaMemcpy(dord.p, hord.data(), hord.size() * sizeof(int), cudaMemcpyHostToDevice));
-    dim3 grid((n * rmax + 255) / 256, 16);
-    extract_lowrank_kernel<<<grid, 256>>>(n, rmax, dranks.as<int>(), dord.as<int>(), A.as<double>(), VR.as<double>(),
-                                          ops->U64.as<double>(), ops->V64.as<double>());
-    M2L_LAUNCH_CHECK("extract_lowrank_kernel");
+    extract_u_kernel<<<dim3((n * rmax + 255) / 256, 16), 256>>>(n, rmax, dranks.as<int>(), dord.as<int>(),
+                                                                  pm.as<int>(), B.as<double>(), ops->U64.as<double>());
+    M2L_LAUNCH_CHECK("extract_u_kernel");
+    apply_q_kernel<<<dim3((rmax + kQWarps - 1) / kQWarps, 16), kQWarps * 32, (size_t)kQWarps * n * sizeof(double)>>>(
+        n, rmax, dranks.as<int>(), dord.as<int>(), A.as<double>(), vh.as<double>(), bt.as<double>(),
+        VJ.as<double>(), ops->V64.as<double>());
+    M2L_LAUNCH_CHECK("apply_q_kernel");
     M2L_CUDA(cudaDeviceSynchronize());
     return M2L_OK;
 }
