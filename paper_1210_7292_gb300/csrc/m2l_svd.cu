@@ -22,8 +22,9 @@
 // rounding noise of the dot products, and far below what changes a singular
 // value the truncation sees (a pair orthogonal to tol perturbs the column
 // norms by O(tol^2)).  The smooth kernels' operators have strongly graded
-// spectra and nearly parallel columns: they take 25-50 sweeps (ell 4-8), so
-// the sweep limit is 100.
+// spectra and nearly parallel columns: taken as they are they need 25-50
+// sweeps (ell 4-8), so the sweep limit is 100; step a1 hands over the R factor
+// of a pivoted QR instead, which converges in 7-11.
 #include <math.h>
 
 #include <algorithm>
