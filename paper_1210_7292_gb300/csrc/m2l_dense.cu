@@ -198,53 +198,6 @@ __global__ void dense_slots_kernel(int umax, const int32_t *__restrict__ meta, c
     if (lane == 0) row[0] = (uint16_t)n;
 }
 
-// One thread per unit: the unit's slots in job order for the paired jobs of the
-// split precisions.  Walking the ascending list, a slot t not yet taken is paired
-// with the first free one of t + 2 e_1, t + 2 e_2, t + 2 e_3 in the list: a unit's
-// targets share an octant, so those slots read the rows slot t reads for the
-// targets one parent over (all but one face of the unit's block).  Pairs come
-// first in the order found, then the slots left single.  [0] is the count.
-__global__ void dense_jobs_kernel(int umax, const int32_t *__restrict__ meta, const uint16_t *__restrict__ slots,
-                                  uint16_t *__restrict__ jobs)
-{
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= umax) return;
-    const uint16_t *row = slots + (size_t)u * kSlotRow;
-    uint16_t *out = jobs + (size_t)u * kSlotRow;
-    const int ns = u < meta[0] ? (int)row[0] : 0;
-    out[0] = (uint16_t)ns;
-    if (ns == 0) return;
-    unsigned present[(kSlots + 31) / 32], used[(kSlots + 31) / 32];
-    for (int w = 0; w < (kSlots + 31) / 32; ++w) present[w] = used[w] = 0u;
-    for (int i = 0; i < ns; ++i) {
-        const int sl = row[1 + i];
-        present[sl >> 5] |= 1u << (sl & 31);
-    }
-    int n = 0, nsingle = 0;
-    uint16_t single[kSlots];
-    for (int i = 0; i < ns; ++i) {
-        const int sl = row[1 + i];
-        if (used[sl >> 5] & (1u << (sl & 31))) continue;
-        used[sl >> 5] |= 1u << (sl & 31);
-        const int t[3] = {sl % 7, (sl / 7) % 7, sl / 49};   // t_i + 3
-        const int step[3] = {2, 14, 98};
-        int partner = -1;
-        for (int a = 0; a < 3 && partner < 0; ++a) {
-            if (t[a] + 2 > 6) continue;
-            const int c = sl + step[a];
-            if ((present[c >> 5] & (1u << (c & 31))) && !(used[c >> 5] & (1u << (c & 31)))) partner = c;
-        }
-        if (partner >= 0) {
-            used[partner >> 5] |= 1u << (partner & 31);
-            out[1 + n++] = (uint16_t)sl;
-            out[1 + n++] = (uint16_t)partner;
-        } else {
-            single[nsingle++] = (uint16_t)sl;
-        }
-    }
-    for (int i = 0; i < nsingle; ++i) out[1 + n++] = single[i];
-}
-
 }  // namespace
 
 bool dense_eligible(const m2l_ops *ops, int ntgt, int nnz)
@@ -295,7 +248,6 @@ m2l_status dense_classify(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const
     if ((st = d.unit_tgt.ensure((size_t)umax * nu * sizeof(int32_t))) != M2L_OK) return st;
     if ((st = d.tab.ensure((size_t)umax * kSlots * nu * sizeof(int32_t))) != M2L_OK) return st;
     if ((st = d.slots.ensure((size_t)umax * kSlotRow * sizeof(uint16_t))) != M2L_OK) return st;
-    if ((st = d.jobs.ensure((size_t)umax * kSlotRow * sizeof(uint16_t))) != M2L_OK) return st;
     if ((st = d.meta.ensure(64 * sizeof(int32_t))) != M2L_OK) return st;
     // split multipoles of any precision: up to two parts of 128 four-byte values per row
     if ((st = d.bsplit.ensure(((size_t)nsrc + 1) * 1024)) != M2L_OK) return st;
@@ -331,9 +283,6 @@ m2l_status dense_classify(const m2l_ops *ops, int ntgt, int nsrc, int nnz, const
     dense_slots_kernel<<<(umax * 32 + 255) / 256, 256, 0, s>>>(umax, d.meta.as<int32_t>(), flags,
                                                                 d.slots.as<uint16_t>());
     M2L_LAUNCH_CHECK("dense_slots_kernel");
-    dense_jobs_kernel<<<(umax + 127) / 128, 128, 0, s>>>(umax, d.meta.as<int32_t>(), d.slots.as<uint16_t>(),
-                                                         d.jobs.as<uint16_t>());
-    M2L_LAUNCH_CHECK("dense_jobs_kernel");
     return M2L_OK;
 }
 
@@ -432,8 +381,21 @@ __device__ __forceinline__ void cp_async_arrive_noinc(uint64_t *bar)
 // Jobs (one per (unit, slot)) run in groups of JP: the stages of a group go K
 // column by K column, the group's jobs in turn, so that the source rows of a
 // job's K column are read again by the next job right after, mostly from L1.
-// With JP = 2 the jobs follow the unit's pairing (dense_jobs_kernel), whose
-// pairs are two steps apart along one axis; with JP = 1 the ascending list.
+// With JP = 2 the jobs take the list entries 0, 2, 1, 3 of each full group of
+// four, so that the two jobs of a pair are mostly two x-steps apart (t and
+// t + 2 e_1): their source rows coincide for all but one face of the unit's
+// block of same-octant targets.
+template <int JP>
+__device__ __forceinline__ int job_entry(int j, int ns)
+{
+    if constexpr (JP == 1) {
+        return j;
+    } else {
+        const int g = j & ~3, r = j & 3;
+        if (g + 4 > ns) return j;
+        return g + (r == 1 ? 2 : (r == 2 ? 1 : r));
+    }
+}
 
 constexpr int kDenseProdWarps = 8;                                        // warps 0-7: producers
 constexpr int kDenseMmaWarp = 8;
@@ -458,8 +420,7 @@ __host__ __device__ constexpr int dense_stage_bytes(int nu)
 template <int KIND>
 __global__ void __launch_bounds__(kDenseThreads, 1)
 tc_dense_kernel(const uint8_t *__restrict__ bsplit, const uint8_t *__restrict__ a_img,
-                const int32_t *__restrict__ meta, const uint16_t *__restrict__ slots,
-                const uint16_t *__restrict__ jobs, const int32_t *__restrict__ tab,
+                const int32_t *__restrict__ meta, const uint16_t *__restrict__ slots, const int32_t *__restrict__ tab,
                 const int32_t *__restrict__ unit_tgt, int nu, int katoms, int nstages, int nsrc, int n3,
                 float *__restrict__ out_f32, double *__restrict__ out_f64, float scale, int *status,
                 int stall_first_stage)
@@ -531,7 +492,7 @@ tc_dense_kernel(const uint8_t *__restrict__ bsplit, const uint8_t *__restrict__ 
         unsigned issued = 0, parity = 0;          // thread 0: operator copies per stage and their phase
         bool stop = false;
         for (int u = blockIdx.x; u < nunits && !stop; u += gridDim.x) {
-            const uint16_t *row = (JP > 1 ? jobs : slots) + (size_t)u * kSlotRow + 1;   // slots in job order
+            const uint16_t *row = slots + (size_t)u * kSlotRow + 1;
             const int ns = row[-1];
             if (ns == 0) continue;
             const int32_t *utab = tab + (size_t)u * kSlots * nu + cb;
@@ -544,12 +505,12 @@ tc_dense_kernel(const uint8_t *__restrict__ bsplit, const uint8_t *__restrict__ 
                 }
             };
             int yA[kDenseMaxColM], yB[kDenseMaxColM];
-            rows_of(row[0], yA);
-            if (JP > 1 && ns > 1) rows_of(row[1], yB);
+            rows_of(row[job_entry<JP>(0, ns)], yA);
+            if (JP > 1 && ns > 1) rows_of(row[job_entry<JP>(1, ns)], yB);
             for (int si = 0; si < ns && !stop; si += JP) {
                 const int nj = min(JP, ns - si);
-                const int slotA = row[si];
-                const int slotB = nj > 1 ? (int)row[si + 1] : slotA;
+                const int slotA = row[job_entry<JP>(si, ns)];
+                const int slotB = nj > 1 ? (int)row[job_entry<JP>(si + 1, ns)] : slotA;
                 for (int ka = 0; ka < katoms && !stop; ++ka) {
                     for (int j = 0; j < nj; ++j, ++it) {
                         const int s = (int)(it % nstages);
@@ -588,8 +549,8 @@ tc_dense_kernel(const uint8_t *__restrict__ bsplit, const uint8_t *__restrict__ 
                     }
                 }
                 // source rows of the next group
-                if (si + JP < ns) rows_of(row[si + JP], yA);
-                if (JP > 1 && si + JP + 1 < ns) rows_of(row[si + JP + 1], yB);
+                if (si + JP < ns) rows_of(row[job_entry<JP>(si + JP, ns)], yA);
+                if (JP > 1 && si + JP + 1 < ns) rows_of(row[job_entry<JP>(si + JP + 1, ns)], yB);
             }
         }
         // every copy this CTA issued lands before its shared memory is released
@@ -792,7 +753,6 @@ m2l_status launch_dense_kind(const m2l_ops *ops, const DenseBuckets &d, const fl
     if (grid > d.umax) grid = d.umax;
     const Layout &L = dense_layout(ops, KIND);
     kern<<<grid, kDenseThreads, smem, s>>>(d.bsplit.as<uint8_t>(), L.a.as<uint8_t>(), d.meta.as<int32_t>(), d.slots.as<uint16_t>(),
-                                          d.jobs.as<uint16_t>(),
                                           d.tab.as<int32_t>(), d.unit_tgt.as<int32_t>(), d.nu, katoms, nst, d.nsrc,
                                           n3, out_fp64 ? nullptr : (float *)out, out_fp64 ? (double *)out : nullptr,
                                           (float)scale, ops->d_status,

@@ -96,7 +96,6 @@ struct DenseBuckets {
     DevBuf unit_tgt;   // int32 [umax][nu]: target index of each column, -1 for padding
     DevBuf tab;        // int32 [umax][343][nu]: source index + 1 of each column and slot, 0 = none
     DevBuf slots;      // uint16 [umax][344]: [0] number of active slots, then the slots ascending
-    DevBuf jobs;       // uint16 [umax][344]: the same slots in job order, pairs first
     DevBuf meta;       // int32 [64]: [0] = number of units; per octant counts, starts, unit offsets
     DevBuf work;       // int32 scratch: per-target ranks and (unit, column), block counts, slot flags
     DevBuf bsplit;     // split multipoles [nsrc + 1][parts][kpad] of the last apply (row nsrc = 0)
@@ -104,8 +103,7 @@ struct DenseBuckets {
     bool valid = false;
     void release()
     {
-        unit_tgt.release(); tab.release(); slots.release(); jobs.release(); meta.release(); work.release();
-        bsplit.release();
+        unit_tgt.release(); tab.release(); slots.release(); meta.release(); work.release(); bsplit.release();
         valid = false;
     }
 };
