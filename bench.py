@@ -1199,7 +1199,9 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
                 "scaling": "strong" if sharded else "weak", "vs_baseline": None,
-                "dtype": {"fp64": "f64"}.get(prec, "f32"),
+                # the arithmetic of the products: BF16 (or TF32) operands, split into three
+                # products for bf16x3 / tf32x3, with FP32 accumulation; FP32 vectors
+                "dtype": {"fp64": "f64", "fp32": "f32"}.get(prec, prec),
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "precision": prec, "levels": list(LEVELS),
                            "interactions_per_step_per_gpu": sum(wl.local_nint.values()),
