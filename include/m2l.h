@@ -57,7 +57,7 @@ typedef enum {
     M2L_ENOMEM = 2,        /* a device allocation failed */
     M2L_ECUDA = 3,         /* a CUDA runtime or library call failed */
     M2L_ETIMEOUT = 4,      /* a bounded device wait gave up (kernel returned early) */
-    M2L_EUNSUPPORTED = 5   /* valid request this build cannot serve (e.g. order too large) */
+    M2L_EUNSUPPORTED = 5   /* valid request the library cannot serve (e.g. order too large) */
 } m2l_status;
 
 /* Kernel functions (Sec. 1; Eq. (33) with the 4*pi factor dropped). */
