@@ -14,6 +14,20 @@
  * matrix-matrix products (Alg. 2, Sec. 4.2.3), optionally on per-operator
  * SVD-compressed factors (Eq. (20), Sec. 4.2).
  *
+ * Steps of the translation, as the entry points below name them:
+ *   a1  the 16 unique operators K_p in FP64 (Eq. (15)), optionally with their
+ *       truncated SVD factors (Eq. (20));
+ *   a2  the 48 symmetry permutations sigma_g and the table t -> (p, g) over
+ *       the 343 transfer vectors (Eqs. (23)-(29), Sec. 4.2.1);
+ *   a3  classification: each list entry's t, its (p, g), and the entries
+ *       bucketed by operator (Alg. 2, first loop);
+ *   a4  gather and permute: W_p[sigma_g(b)][c] = w_Y[b] (Eq. (30), the same
+ *       loop);
+ *   a5  the blocked product F_p = K_p W_p per operator (Eq. (31), Alg. 2,
+ *       second loop);
+ *   a6  un-permute and add into the locals: f[a] += F_p[sigma_g(a)][c]
+ *       (Eq. (32), Alg. 2, third loop).
+ *
  * Conventions shared by every entry point:
  *  - Pointers named "device" are CUDA device pointers owned by the caller;
  *    "host" pointers are ordinary host memory owned by the caller.  The
@@ -230,9 +244,10 @@ m2l_status m2l_apply_level(const m2l_ops *ops, const m2l_level *level, const voi
                            void *locals, int precision, int locals_fp64, void *stream);
 
 /* Adjoint of m2l_apply_level: grad_multipoles[Y] += K_t^T grad_locals[X]
- * over the same pairs.  Since K_{-t} = K_t^T (the kernel is symmetric), this
- * is the forward translation on the transposed list, which the library
- * builds on the device.  grad_locals: [ncells_tgt][ell^3];
+ * over the same pairs.  Since K_{-t} = K_t^T (the kernel is symmetric, and
+ * -t is the transfer vector of the reversed pair, Sec. 3.1), this is the
+ * forward translation on the transposed list, which the library builds on
+ * the device.  grad_locals: [ncells_tgt][ell^3];
  * grad_multipoles: [ncells_src][ell^3], accumulated; types as for apply with
  * the roles of the two arrays exchanged. */
 m2l_status m2l_apply_level_adjoint(const m2l_ops *ops, const m2l_level *level,
